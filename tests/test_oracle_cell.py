@@ -1,0 +1,126 @@
+"""Pins of the oracle's per-cell force and tangent (Eq. internalloadvec, Section 3.1.4) -- CPU."""
+import numpy as np
+import pytest
+
+import latgen
+from oracle import cell as C
+from oracle.assembly import Problem
+
+
+def _case(X, E, dims, mu=1.0, lam=4.0):
+    lat = latgen.tile(X, E, dims)
+    return latgen.LoadCase("t", lat, mu, lam, np.ones(lat.n_cells), 0.1, 1, 1e-3)
+
+
+@pytest.mark.parametrize("which", ["ring", "strut"])
+def test_rigid_motion_zero_residual(which):
+    if which == "ring":
+        case = _case(*latgen.ring_cell(8), (2, 2))
+        R = np.array([[np.cos(0.7), -np.sin(0.7)], [np.sin(0.7), np.cos(0.7)]])
+    else:
+        case = _case(*latgen.strut_cell(6, 0.2), (2, 1, 1))
+        a, b = 0.5, -0.9
+        Rz = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1]])
+        Rx = np.array([[1, 0, 0], [0, np.cos(b), -np.sin(b)], [0, np.sin(b), np.cos(b)]])
+        R = Rz @ Rx
+    prob = Problem(case)
+    X = prob.lat.X
+    u = (X @ R.T - X + 0.3).ravel()
+    assert np.abs(prob.residual(u)).max() < 1e-12
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("s", [0.9, 1.05])
+def test_uniaxial_strain_patch_and_reaction(d, s):
+    X, E = latgen.solid_cell(3, d)
+    dims = (2, 3) if d == 2 else (2, 1, 2)
+    prob = Problem(_case(X, E, dims))
+    lat = prob.lat
+    ax = lat.load_axis
+    u = np.zeros((lat.n_nodes, d))
+    u[:, ax] = (s - 1) * lat.X[:, ax]
+    r = prob.residual(u.ravel()).reshape(-1, d)
+    ext = np.asarray(lat.dims, dtype=float)
+    boundary = np.any((np.abs(lat.X) < 1e-12) | (np.abs(lat.X - ext) < 1e-12), axis=1)
+    assert np.abs(r[~boundary]).max() < 1e-13             # patch test: interior forces vanish
+    P = 1.0 * (s * s - 1) / s + 4.0 * np.log(s) / s      # first Piola P_axis,axis = sigma_axis,axis
+    area = np.prod([ext[k] for k in range(d) if k != ax])
+    top = lat.top_nodes()
+    assert abs(r[top, ax].sum() - P * area) < 1e-12 * max(1, abs(P))
+
+
+def _linear_q1_stiffness(h, d, mu, lam):
+    """Textbook B-matrix (Voigt) stiffness of an axis-aligned cube element of side h."""
+    g = 1 / np.sqrt(3)
+    nodes = latgen.solid_cell(1, d)[0] * 2 - 1                   # local node positions in [-1,1]^d
+    pts = np.array(np.meshgrid(*[[-g, g]] * d, indexing="ij")).reshape(d, -1).T
+    nv = 3 if d == 2 else 6
+    Cv = np.zeros((nv, nv))
+    Cv[:d, :d] = lam
+    Cv[range(d), range(d)] += 2 * mu
+    Cv[range(d, nv), range(d, nv)] = mu
+    shear = [(0, 1)] if d == 2 else [(1, 2), (0, 2), (0, 1)]
+    K = np.zeros((2 ** d * d, 2 ** d * d))
+    for p in pts:
+        Bm = np.zeros((nv, 2 ** d * d))
+        for a, na in enumerate(nodes):
+            grad = np.array([na[k] * np.prod([1 + na[m] * p[m] for m in range(d) if m != k])
+                             for k in range(d)]) / 2 ** d * (2 / h)
+            for k in range(d):
+                Bm[k, a * d + k] = grad[k]
+            for v, (i, j) in enumerate(shear):
+                Bm[d + v, a * d + i] = grad[j]
+                Bm[d + v, a * d + j] = grad[i]
+        K += Bm.T @ Cv @ Bm * (h / 2) ** d
+    return K
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_tangent_at_rest_is_linear_elastic(d):
+    X, E = latgen.solid_cell(1, d)
+    cell = C.RefCell(X * 0.5, E)          # one element of side 0.5
+    K = cell.dense(C.tangent(cell, np.zeros((1, 2 ** d, d)), np.array([1.3]), 4.0)[0])
+    ref = _linear_q1_stiffness(0.5, d, 1.3, 4.0)
+    assert np.abs(K - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("which", ["ring", "strut"])
+def test_tangent_central_difference_and_symmetry(which):
+    X, E = latgen.ring_cell(4) if which == "ring" else latgen.strut_cell(4, 0.3)
+    cell = C.RefCell(X, E)
+    rng = np.random.default_rng(1)
+    u = 0.01 * rng.uniform(-1, 1, (1, cell.n_nodes, cell.d))
+    v = rng.uniform(-1, 1, (1, cell.n_nodes, cell.d))
+    mu = np.array([1.1])
+    K = cell.dense(C.tangent(cell, u, mu, 4.0)[0])
+    assert np.abs(K - K.T).max() < 1e-13 * np.abs(K).max()
+    Kv = K @ v.ravel()
+    errs = []
+    for h in (1e-4, 5e-5):
+        fd = (C.internal_force(cell, u + h * v, mu, 4.0) - C.internal_force(cell, u - h * v, mu, 4.0))
+        errs.append(np.abs(fd.ravel() / (2 * h) - Kv).max())
+    assert errs[1] < 1e-4 * np.abs(Kv).max()
+    assert 3.5 < errs[0] / errs[1] < 4.5                   # O(h^2) central difference
+
+
+def test_snapshot_is_reduced_rule_tangent():
+    X, E = latgen.ring_cell(4)
+    cell = C.RefCell(X, E)
+    rng = np.random.default_rng(2)
+    u = 0.02 * rng.uniform(-1, 1, (3, cell.n_nodes, 2))
+    T = C.snapshots(cell, u, np.ones(3), 4.0)
+    assert T.shape == (cell.nnz, 3)
+    # one-point rule: the element matrix is the centre-point integrand times the element area
+    Kbar = C.tangent(cell, u, np.ones(3), 4.0, reduced=True)
+    assert np.array_equal(T, Kbar.T)
+    Kfull = C.tangent(cell, u, np.ones(3), 4.0)
+    rel = np.abs(Kbar - Kfull).max() / np.abs(Kfull).max()
+    assert 1e-4 < rel < 0.5            # an under-integrated, but close, tangent
+
+
+def test_pattern_covers_element_pairs():
+    X, E = latgen.ring_cell(8)
+    cell = C.RefCell(X, E)
+    assert cell.nnz == 2496
+    X, E = latgen.ring_cell(16)
+    assert C.RefCell(X, E).nnz == 9600
