@@ -10,8 +10,9 @@ Readings where the paper is silent:
 * load step k prescribes the top face at -(k / n_steps) * strain * H along the load axis;
 * predictor: step 1 starts from the affine field u_axis = (delta_1 / H) X_axis, later steps
   from the linear extrapolation 2 u_{k-1} - u_{k-2}; Dirichlet values are then overwritten;
-* r0 is the predictor's residual; an absolute floor of 1e-14 ||f_int(u)||_2 (all DOFs,
-  reactions included) stops the iteration when r0 itself is at round-off level.
+* r0 is the predictor's residual; an absolute floor of 1e-12 ||f_int(u)||_2 (all DOFs,
+  reactions included) stops the iteration once the free residual is at round-off level
+  (below it Armijo cannot find a decrease: the residual only changes by rounding).
 """
 import dataclasses
 
@@ -55,7 +56,7 @@ def newton_solve(prob, u0, tol=1e-8, max_it=50, mu=None, solver=None):
     rn = np.linalg.norm(r[free])
     r0 = rn
     hist, ls = [rn], []
-    floor = 1e-14 * max(np.linalg.norm(r), 1e-300)
+    floor = 1e-12 * max(np.linalg.norm(r), 1e-300)
     it = 0
     while rn > tol * r0 and rn > floor and it < max_it:
         K = prob.tangent(u, mu)
@@ -81,7 +82,7 @@ def newton_solve(prob, u0, tol=1e-8, max_it=50, mu=None, solver=None):
         u, r, rn = ut, rt, rtn
         ls.append(m)
         hist.append(rn)
-        floor = 1e-14 * max(np.linalg.norm(r), 1e-300)
+        floor = 1e-12 * max(np.linalg.norm(r), 1e-300)
         it += 1
     return u, NewtonReport(it, hist, ls, bool(rn <= tol * r0 or rn <= floor))
 

@@ -1,0 +1,167 @@
+// Reduced tangent action (Eq. romstiffnessmatrix):  Y[:, s] = sum_r alpha_r^s K^r X[:, s]
+// on cell-stacked multivectors [n_loc][n_cells], and the per-cell action of the plain path
+// (every cell principal, alpha = I: Y[:, s] = K^s X[:, s]).
+//
+// Layout and mapping.  One thread per (cell s, local node a) computes the d outputs of node a.
+// A warp holds 32 consecutive cells at the same node, so the reads of X and writes of Y are
+// coalesced 32-cell rows, while the principal values K^r_ab are warp-uniform (one broadcast
+// load per warp, L1 resident: all principals together are a few hundred KB).  The alpha
+// combination is fused: per node block (a, b) the thread forms sum_r alpha_r^s K^r_ab in
+// registers and multiplies by x_b once.
+//
+// FETI mode (Section 3.3.1): the input is the remaining part of a saddle-point vector, the corner
+// values come from the global primal vector through the cell's primal map; outputs at fixed
+// local DOFs are zeroed, outputs at corner rows are kept for the primal assembly.
+#include "common.cuh"
+
+namespace {
+
+struct ApplyArgs {
+  int n_cells, nn;
+  int64_t nnz;
+  const int* blk_ptr;
+  const int* blk_col;
+  const int* corner_of_node;  // FETI
+  const int* pidx;            // FETI [n_cells][n_P]
+  const uint8_t* loc_fixed;   // FETI [n_loc][n_cells]
+  const double* xP;           // FETI primal vector
+};
+
+template <typename T, int D, bool FETI>
+__device__ __forceinline__ void load_xb(const ApplyArgs& A, const T* __restrict__ X, int s, int b,
+                                        T (&xb)[D]) {
+  if (FETI) {
+    const int c = A.corner_of_node[b];
+    if (c >= 0) {
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        const int p = A.pidx[(size_t)s * (D << D) + c * D + j];
+        xb[j] = p >= 0 ? (T)A.xP[p] : T(0);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const size_t e = (size_t)(b * D + j) * A.n_cells + s;
+    T v = X[e];
+    if (FETI && A.loc_fixed[e]) v = T(0);
+    xb[j] = v;
+  }
+}
+
+template <typename T, int D, bool FETI>
+__device__ __forceinline__ void store_ya(const ApplyArgs& A, T* __restrict__ Y, int s, int a,
+                                         const T (&ya)[D]) {
+  const bool corner = FETI && A.corner_of_node[a] >= 0;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    const size_t e = (size_t)(a * D + i) * A.n_cells + s;
+    T v = ya[i];
+    if (FETI && !corner && A.loc_fixed[e]) v = T(0);
+    Y[e] = v;
+  }
+}
+
+template <typename T, int D, bool FETI>
+__global__ void __launch_bounds__(256)
+    k_apply_reduced(ApplyArgs A, int n_r, const T* __restrict__ Kp, const T* __restrict__ alpha,
+                    const T* __restrict__ X, T* __restrict__ Y) {
+  const int s = blockIdx.x * 32 + threadIdx.x;
+  const int a = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a >= A.nn) return;
+  const bool live = s < A.n_cells;
+  const int sc = live ? s : A.n_cells - 1;  // keep the warp converged for uniform loads
+  T y[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) y[i] = T(0);
+  for (int bi = A.blk_ptr[a]; bi < A.blk_ptr[a + 1]; ++bi) {
+    const int b = A.blk_col[bi];
+    T xb[D];
+    load_xb<T, D, FETI>(A, X, sc, b, xb);
+    T kt[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) kt[i][j] = T(0);
+    for (int r = 0; r < n_r; ++r) {
+      const T al = alpha[(size_t)r * A.n_cells + sc];
+      const T* kb = Kp + (size_t)r * A.nnz + (size_t)bi * D * D;
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) kt[i][j] = fma(al, __ldg(kb + i * D + j), kt[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) y[i] = fma(kt[i][j], xb[j], y[i]);
+  }
+  if (live) store_ya<T, D, FETI>(A, Y, s, a, y);
+}
+
+// plain path: each cell its own K^s, [n_cells][nnz]
+template <typename T, int D, bool FETI>
+__global__ void __launch_bounds__(256)
+    k_apply_percell(ApplyArgs A, const T* __restrict__ Kall, const T* __restrict__ X, T* __restrict__ Y) {
+  const int s = blockIdx.x * 32 + threadIdx.x;
+  const int a = blockIdx.y * blockDim.y + threadIdx.y;
+  if (a >= A.nn || s >= A.n_cells) return;
+  const T* K = Kall + (size_t)s * A.nnz;
+  T y[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) y[i] = T(0);
+  for (int bi = A.blk_ptr[a]; bi < A.blk_ptr[a + 1]; ++bi) {
+    const int b = A.blk_col[bi];
+    T xb[D];
+    load_xb<T, D, FETI>(A, X, s, b, xb);
+    const T* kb = K + (size_t)bi * D * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) y[i] = fma(kb[i * D + j], xb[j], y[i]);
+  }
+  store_ya<T, D, FETI>(A, Y, s, a, y);
+}
+
+template <typename T, int D, bool FETI>
+void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T* X, T* Y) {
+  dim3 blk(32, 8);
+  dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
+  if (h->force_all)
+    k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y);
+  else
+    k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y);
+  LAT_CHECK_LAUNCH();
+}
+
+template <typename T>
+void dispatch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T* X, T* Y, bool feti) {
+  if (h->dim == 2) {
+    if (feti) launch<T, 2, true>(h, A, Kp, alpha, X, Y);
+    else launch<T, 2, false>(h, A, Kp, alpha, X, Y);
+  } else {
+    if (feti) launch<T, 3, true>(h, A, Kp, alpha, X, Y);
+    else launch<T, 3, false>(h, A, Kp, alpha, X, Y);
+  }
+}
+
+}  // namespace
+
+void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti) {
+  LAT_REQUIRE(h->n_r > 0 && h->Kp.p, LAT_EINVAL, "no principal cells selected");
+  ApplyArgs A{h->n_cells, h->n_nodes_cell, h->nnz, h->blk_ptr.p, h->blk_col.p,
+              h->corner_of_node.p, h->pidx.p, h->loc_fixed.p, xP};
+  if (dtype == 0) {
+    dispatch<double>(h, A, h->Kp.p, h->alpha.p, (const double*)x, (double*)y, feti);
+  } else {
+    LAT_REQUIRE(h->Kp32.p && (h->force_all || h->alpha32.p), LAT_EINVAL,
+                "FP32 action needs a handle created in a mixed precision mode");
+    dispatch<float>(h, A, h->Kp32.p, h->alpha32.p, (const float*)x, (float*)y, feti);
+  }
+}
+
+extern "C" lat_status apply_reduced_tangent(lat_handle h, const void* x, void* y, int32_t dtype) {
+  if (!h || !x || !y || (dtype != 0 && dtype != 1)) return LAT_EINVAL;
+  return guard(h, [&] { run_apply(h, x, y, dtype, nullptr, false); });
+}

@@ -1,0 +1,286 @@
+// Internal definitions shared by the translation units of liblattice.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "lattice.h"
+
+// ------------------------------------------------------------------------------------------
+// error handling: every entry point returns lat_status, the message goes to h->err
+// ------------------------------------------------------------------------------------------
+struct LatError {
+  lat_status code;
+  std::string msg;
+};
+
+#define LAT_CUDA(call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw LatError{e_ == cudaErrorMemoryAllocation ? LAT_ENOMEM : LAT_ECUDA,             \
+                     std::string(#call) + ": " + cudaGetErrorString(e_)};                  \
+  } while (0)
+
+#define LAT_CHECK_LAUNCH() LAT_CUDA(cudaGetLastError())
+
+#define LAT_REQUIRE(cond, code, text)                                                      \
+  do {                                                                                     \
+    if (!(cond)) throw LatError{code, text};                                               \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// device buffers owned by the handle
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void ensure(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    LAT_CUDA(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void upload(const std::vector<T>& v, cudaStream_t st) {
+    ensure(v.size());
+    if (!v.empty())
+      LAT_CUDA(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// the handle
+// ------------------------------------------------------------------------------------------
+struct lat_ctx {
+  // sizes
+  int dim = 0, nen = 0, n_cells = 0, n_nodes_cell = 0, n_el = 0, n_loc = 0, n_blk = 0;
+  int64_t nnz = 0, n_glob_nodes = 0, n_dof = 0;
+  int nq[2] = {0, 0};  // [0] full rule, [1] reduced rule (per element)
+  double mu = 0, lam = 0;
+  lat_precision prec = LAT_FP64;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int n_sm = 0;
+
+  // reference cell
+  DBuf<double> gradX[2], W[2];  // [n_el][nq][nen][dim], [n_el][nq]
+  DBuf<int> elems;              // [n_el][nen]
+  DBuf<int> elem_blk;           // [n_el][nen][nen] block index of (a, b)
+  std::vector<int> color_start; // host offsets into color_elems
+  DBuf<int> color_elems;
+  DBuf<int> blk_ptr, blk_col;   // node-block CSR of the local pattern
+  std::vector<int> h_blk_ptr, h_blk_col;
+
+  // lattice
+  DBuf<int> cell_nodes;               // [n_cells][n_nodes_cell]
+  DBuf<double> mu_cell;               // [n_cells] mu * theta_s
+  std::vector<double> h_mu_scale;
+  DBuf<int> copy_ptr, copy_idx;       // global node -> copies s*n_nodes_cell + a
+  DBuf<uint8_t> dof_fixed;            // [n_dof]
+  DBuf<double> dir_unit, aff_unit;    // [n_dof]
+  std::vector<uint8_t> h_dof_fixed;
+
+  // FETI-DP structure
+  int n_P = 0, n_R = 0;               // local primal (corner) / remaining dofs
+  DBuf<int> corner_of_node;           // [n_nodes_cell] corner id or -1
+  DBuf<int> rdofs, pdofs;             // [n_R], [n_P] local dof ids
+  DBuf<int> rpos;                     // [n_loc] position in rdofs or -1
+  DBuf<int> pidx;                     // [n_cells][n_P] free global primal index or -1
+  int64_t n_primal = 0, n_lambda = 0, n_krylov = 0;
+  DBuf<int> p_copy_ptr, p_copy;       // primal dof -> local entries k*n_cells+s (P rows)
+  DBuf<uint8_t> loc_fixed;            // [n_loc][n_cells] 1 = fixed local entry (or P row)
+  DBuf<int> lam_p, lam_m;             // [n_lambda] local entries of the +/- copies
+  DBuf<int> dual_entry, dual_l1, dual_l2;  // dual copies and their multipliers (+-(l+1), 0 = none)
+  DBuf<double> dual_scale;            // [n_dual] 1/multiplicity of the node
+  int64_t n_dual = 0;
+  int n_classes = 0;
+  DBuf<int> cell_class;               // [n_cells] boundary-condition class
+  std::vector<int> class_rep;         // representative cell per class
+  DBuf<int> coarse_ptr, coarse_src;   // coarse matrix entries -> (cell, i, j) contributions
+  DBuf<int> coarse_row, coarse_col;
+
+  // selection state
+  int n_r = 0;
+  bool force_all = false;
+  DBuf<int> S;                        // [n_r]
+  DBuf<double> alpha;                 // [n_r][n_cells]
+  DBuf<float> alpha32;
+  DBuf<double> Kp;                    // [n_r][nnz]
+  DBuf<float> Kp32;
+  // greedy workspaces
+  DBuf<double> g_delta, g_Z, g_beta, g_inf, g_nrm2, g_norms, g_part, g_maxres;
+  DBuf<int> g_state;                  // [0] done, [1] n_r, [2] s_next
+  DBuf<double> g_scale;
+  // assembly workspaces
+  DBuf<double> f_cells, r_glob, minJ_cell, T;
+  DBuf<int> negJ;
+
+  // solver state
+  int n_keys = 0;
+  DBuf<int> key_of_cell, key_slot, perm, seg_ptr, tile_seg, tile_c0, key_list, solver_int;
+  DBuf<double> delta_cell, c_cell;    // per-cell inverse weight and scale
+  DBuf<double> G, Phi, Sloc;          // [n_keys][n_R][n_R], [n_keys][n_R][n_P], [n_keys][n_P][n_P]
+  DBuf<float> G32;
+  DBuf<__nv_bfloat16> G16;
+  DBuf<double> KRP, Coarse, CoarseInv;
+  DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
+  DBuf<float> x32, y32;               // mixed-precision local vectors
+  DBuf<double> kv_tmp[6];             // saddle-point sized temporaries
+  DBuf<double> V, Zk, Hh, gmres_small, dots_part;
+  DBuf<int> flag;
+  DBuf<double> red_part;            // reduction scratch
+  int max_tiles = 0;
+  bool indefinite = false;
+  bool verbose = false;               // LATTICE_VERBOSE=1: per-iteration log on stderr           // some local or coarse pivot was negative
+  double *h_pinned = nullptr;          // small pinned host scratch
+};
+
+// run f, converting LatError and std exceptions into a status and h->err
+template <typename F>
+static lat_status guard(lat_ctx* h, F&& f) {
+  try {
+    f();
+    return LAT_OK;
+  } catch (const LatError& e) {
+    if (h) h->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    if (h) h->err = e.what();
+    return LAT_EINVAL;
+  }
+}
+
+// element colours passed by value to the per-cell kernels
+struct ColorTable {
+  int n;
+  int start[33];
+};
+
+// ------------------------------------------------------------------------------------------
+// small helpers
+// ------------------------------------------------------------------------------------------
+static inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <int D>
+__device__ __forceinline__ double det_inv(const double (&F)[D][D], double (&Fi)[D][D]);
+
+template <>
+__device__ __forceinline__ double det_inv<2>(const double (&F)[2][2], double (&Fi)[2][2]) {
+  double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+  double r = 1.0 / J;
+  Fi[0][0] = F[1][1] * r;
+  Fi[0][1] = -F[0][1] * r;
+  Fi[1][0] = -F[1][0] * r;
+  Fi[1][1] = F[0][0] * r;
+  return J;
+}
+
+template <>
+__device__ __forceinline__ double det_inv<3>(const double (&F)[3][3], double (&Fi)[3][3]) {
+  double c00 = F[1][1] * F[2][2] - F[1][2] * F[2][1];
+  double c01 = F[1][2] * F[2][0] - F[1][0] * F[2][2];
+  double c02 = F[1][0] * F[2][1] - F[1][1] * F[2][0];
+  double J = F[0][0] * c00 + F[0][1] * c01 + F[0][2] * c02;
+  double r = 1.0 / J;
+  Fi[0][0] = c00 * r;
+  Fi[1][0] = c01 * r;
+  Fi[2][0] = c02 * r;
+  Fi[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * r;
+  Fi[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * r;
+  Fi[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * r;
+  Fi[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * r;
+  Fi[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * r;
+  Fi[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * r;
+  return J;
+}
+
+// deterministic block reductions (fixed shape, fixed order)
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+// block-wide sum for blockDim.x a multiple of 32 (<= 1024); all threads get the result
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* sh /* >= 32 */) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T out = sh[0];
+  __syncthreads();
+  return out;
+}
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sh[threadIdx.x] : T(-1e300);
+  if (wid == 0) t = warp_max(t);
+  if (threadIdx.x == 0) sh[0] = t;
+  __syncthreads();
+  T out = sh[0];
+  __syncthreads();
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------
+// cross-unit launchers (defined in the .cu files)
+// ------------------------------------------------------------------------------------------
+void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_glob,
+                  double* min_detF_host, bool* negJ);
+void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, int n_sel,
+                 double* K_out, bool* negJ);
+void run_tangent_apply_exact(lat_ctx* h, const double* u_glob, const double* v_glob,
+                             double* y_glob);
+void run_grad_mu(lat_ctx* h, const double* u_glob, const double* w_glob, double* grad);
+double run_norm_free(lat_ctx* h, const double* r_glob);
+double run_norm_all(lat_ctx* h, const double* r_glob);
+double run_dot_fixed(lat_ctx* h, const double* a, const double* b);
+void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double eps, int max_nr,
+                int* S_out, int* n_r_out, double* alpha_out, double* beta_out, double* Z_out,
+                double* max_res_host);
+void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti);
+void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
+void run_feti_operator(lat_ctx* h, const double* v, double* w);
+void run_kinv(lat_ctx* h, const double* v, double* w);
+void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters);
+int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o, double* rel_out);
+void run_feti_to_global(lat_ctx* h, const double* v, double* u);
+void run_feti_from_global(lat_ctx* h, const double* u, double* v, bool split);
+void run_axpy(lat_ctx* h, int64_t n, double a, const double* x, double* y);
+void run_f2d(lat_ctx* h, int64_t n, const float* x, double* y);
+void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed);
+void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w);
+void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool force_all);

@@ -1,0 +1,1372 @@
+// FETI-DP saddle-point operator, the block preconditioner of Eq. (ifetidp_precond) built on the
+// principal cells, FGMRES, Newton-Raphson with Armijo backtracking and the adjoint gradient.
+//
+// Saddle-point vectors (Section 3.3.1) are [local part | primal part | multipliers]:
+//   local part  [n_loc][n_cells]  remaining (interior + dual) DOFs of every cell; corner rows and
+//                                 Dirichlet rows are kept at zero,
+//   primal part [n_primal]        free corner DOFs, assembled globally,
+//   multipliers [n_lambda]        one per pair of consecutive copies of a free dual DOF.
+// The operator is A = [K~ B^T; B 0] with K~ the partially assembled reduced tangent (the cell-wise
+// action of Eq. romstiffnessmatrix with the primal values gathered at the corners).
+//
+// Preconditioner (Eq. ifetidp_precond):
+//   t = K^-rom v_u;  y = v_l - B t;  z_l = -PCG_k(B K^-rom B^T, y);  w_u = K^-rom (v_u - B^T z_l)
+// K^-rom is the FETI-DP partially assembled inverse built from the principal cells: every cell s
+// is tied to one principal r(s) (largest coefficient alpha_r^s) and its boundary-condition class,
+// and uses that principal's exact local pieces
+//   G^r = (K_RR^r)^{-1},  Phi^r = -G^r K_RP^r,  S^r = K_PP^r + K_RP^{rT} Phi^r,
+// scaled by c_s = sum_r alpha_r^s (K^s ~ c_s K^{r(s)}): K_RR^{s,-1} ~ G^{r(s)} / c_s,
+// Phi^s ~ Phi^{r(s)}, S^s ~ c_s S^{r(s)}.  The coarse matrix sum_s A_P^{sT} S^s A_P^s is FP64 and
+// inverted explicitly.  With every cell principal this is the exact partially assembled inverse.
+// The interface sub-preconditioner is k PCG iterations on B K^-rom B^T with the lumped
+// preconditioner B_D K~_dd B_D^T (multiplicity scaling).
+#include <algorithm>
+#include <cfloat>
+#include <chrono>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// elementwise and reduction kernels on saddle-point vectors
+// ---------------------------------------------------------------------------------------------
+constexpr int kRed = 512;
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+
+// PCG step lengths with a breakdown guard: sc[0] rz, sc[1] pq, sc[2] rz_new, sc[3] alpha,
+// sc[4] beta, sc[5] frozen (once p.q <= 0 or r.z <= 0 the iteration stops updating)
+__global__ void k_pcg_alpha(double* sc) {
+  const bool ok = sc[5] == 0.0 && sc[1] > 0.0 && sc[0] > 0.0;
+  if (!ok) sc[5] = 1.0;
+  sc[3] = ok ? sc[0] / sc[1] : 0.0;
+}
+__global__ void k_pcg_beta(double* sc) {
+  const bool ok = sc[5] == 0.0 && sc[2] > 0.0 && sc[0] > 0.0;
+  if (!ok) sc[5] = 1.0;
+  sc[4] = ok ? sc[2] / sc[0] : 0.0;
+  sc[0] = sc[2];
+}
+// y += sgn * a[0] * x
+__global__ void k_axpy_s(int64_t n, const double* __restrict__ a, double sgn, const double* __restrict__ x,
+                         double* __restrict__ y) {
+  const double c = sgn * a[0];
+  if (c == 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += c * x[i];
+}
+// p = z + b[0] p  (p left unchanged when the iteration is frozen)
+__global__ void k_xpby_s(int64_t n, const double* __restrict__ z, const double* __restrict__ b,
+                         const double* __restrict__ frozen, double* __restrict__ p) {
+  if (frozen[0] != 0.0) return;
+  const double c = b[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + c * p[i];
+}
+
+__global__ void k_dot_part(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ part) {
+  __shared__ double red[32];
+  double v = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v += a[i] * b[i];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+}
+
+__global__ void k_sum_part(int n, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double red[32];
+  double v = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) out[0] = v;
+}
+
+// partial dots of w against the first m vectors of V (stride n): part[i][block]
+__global__ void k_multidot_part(int64_t n, int m, const double* __restrict__ V, const double* __restrict__ w,
+                                double* __restrict__ part) {
+  __shared__ double red[32];
+  for (int i = 0; i < m; ++i) {
+    const double* vi = V + (size_t)i * n;
+    double v = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+      v += vi[k] * w[k];
+    v = block_sum(v, red);
+    if (threadIdx.x == 0) part[(size_t)i * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+__global__ void k_multidot_final(int nb, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  double v = 0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += part[(size_t)i * nb + b];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) out[i] = v;
+}
+
+// w -= sum_i h[i] V_i  (and accumulate into hacc when given)
+__global__ void k_multi_axpy(int64_t n, int m, const double* __restrict__ V, const double* __restrict__ hcoef,
+                             double sgn, double* __restrict__ w) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double v = w[k];
+    for (int i = 0; i < m; ++i) v += sgn * hcoef[i] * V[(size_t)i * n + k];
+    w[k] = v;
+  }
+}
+
+__global__ void k_scale_dev(int64_t n, const double* __restrict__ x, const double* __restrict__ nrm2,
+                            double* __restrict__ y) {
+  const double s = 1.0 / sqrt(nrm2[0]);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// FETI-DP index kernels
+// ---------------------------------------------------------------------------------------------
+// yP[p] = (accumulate ? yP[p] : 0) + sum over the copies of p of loc[entry]
+__global__ void k_primal_assemble(int64_t n_primal, const int* __restrict__ pptr, const int* __restrict__ pc,
+                                  const double* __restrict__ loc, double* __restrict__ yP, int accumulate) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_primal) return;
+  double v = accumulate ? yP[p] : 0.0;
+  for (int c = pptr[p]; c < pptr[p + 1]; ++c) v += loc[pc[c]];
+  yP[p] = v;
+}
+
+// zero the corner rows of a local vector (entries listed per primal dof) -- all corner rows
+__global__ void k_zero_rows(int n_cells, int n_P, const int* __restrict__ pdofs, double* __restrict__ loc) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_cells) return;
+  for (int j = 0; j < n_P; ++j) loc[(size_t)pdofs[j] * n_cells + s] = 0.0;
+}
+
+// lambda_l = x[p_l] - x[m_l]  (B x), or lambda += ...
+__global__ void k_jump(int64_t L, const int* __restrict__ lp, const int* __restrict__ lm,
+                       const double* __restrict__ x, double a, double* __restrict__ lam, int accumulate) {
+  int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double v = a * (x[lp[l]] - x[lm[l]]);
+  lam[l] = accumulate ? lam[l] + v : v;
+}
+
+// y[dual entry] += a * (B^T lambda) (optionally scaled by 1/multiplicity)
+__global__ void k_jump_t(int64_t nd, const int* __restrict__ de, const int* __restrict__ l1,
+                         const int* __restrict__ l2, const double* __restrict__ scale,
+                         const double* __restrict__ lam, double a, double* __restrict__ y) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nd) return;
+  double v = 0;
+  int c1 = l1[e], c2 = l2[e];
+  if (c1) v += (c1 > 0 ? 1.0 : -1.0) * lam[abs(c1) - 1];
+  if (c2) v += (c2 > 0 ? 1.0 : -1.0) * lam[abs(c2) - 1];
+  if (scale) v *= scale[e];
+  y[de[e]] += a * v;
+}
+
+// scaled jump  lambda_l = (x[p] * s_p - x[m] * s_m)  with per-entry scaling gathered from a
+// dense scale array indexed like the local vector
+__global__ void k_jump_scaled(int64_t L, const int* __restrict__ lp, const int* __restrict__ lm,
+                              const double* __restrict__ x, const double* __restrict__ wloc,
+                              double* __restrict__ lam) {
+  int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  lam[l] = x[lp[l]] * wloc[lp[l]] - x[lm[l]] * wloc[lm[l]];
+}
+
+__global__ void k_fill_dual_weights(int64_t nd, const int* __restrict__ de, const double* __restrict__ sc,
+                                    double* __restrict__ wloc) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nd) wloc[de[e]] = sc[e];
+}
+
+// saddle-point vector -> global vector: corners from the primal part, other DOFs the mean of
+// their copies, Dirichlet DOFs zero
+__global__ void k_to_global(int64_t n_nodes, int D, int nn, int n_cells, int n_P, const int* __restrict__ cptr,
+                            const int* __restrict__ cidx, const int* __restrict__ corner_of_node,
+                            const int* __restrict__ pidx, const uint8_t* __restrict__ fixed,
+                            const double* __restrict__ loc, const double* __restrict__ xP,
+                            double* __restrict__ u) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_nodes) return;
+  const int c0 = cptr[g], c1 = cptr[g + 1];
+  const int s0 = cidx[c0] / nn, a0 = cidx[c0] % nn;
+  const int corner = corner_of_node[a0];
+  for (int i = 0; i < D; ++i) {
+    double v = 0;
+    if (!fixed[g * D + i]) {
+      if (corner >= 0) {
+        const int p = pidx[(size_t)s0 * n_P + corner * D + i];
+        v = p >= 0 ? xP[p] : 0.0;
+      } else {
+        for (int c = c0; c < c1; ++c) {
+          const int s = cidx[c] / nn, a = cidx[c] % nn;
+          v += loc[(size_t)(a * D + i) * n_cells + s];
+        }
+        v /= (double)(c1 - c0);
+      }
+    }
+    u[g * D + i] = v;
+  }
+}
+
+// global vector -> saddle-point vector (split: local values divided by the multiplicity so that
+// the copies sum to the global value)
+__global__ void k_from_global(int64_t n_nodes, int D, int nn, int n_cells, int n_P, const int* __restrict__ cptr,
+                              const int* __restrict__ cidx, const int* __restrict__ corner_of_node,
+                              const int* __restrict__ pidx, const uint8_t* __restrict__ fixed,
+                              const double* __restrict__ u, int split, double* __restrict__ loc,
+                              double* __restrict__ xP) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= n_nodes) return;
+  const int c0 = cptr[g], c1 = cptr[g + 1];
+  const int s0 = cidx[c0] / nn, a0 = cidx[c0] % nn;
+  const int corner = corner_of_node[a0];
+  for (int i = 0; i < D; ++i) {
+    const bool fx = fixed[g * D + i];
+    const double v = fx ? 0.0 : u[g * D + i];
+    if (corner >= 0) {
+      const int p = pidx[(size_t)s0 * n_P + corner * D + i];
+      if (p >= 0) xP[p] = v;
+      for (int c = c0; c < c1; ++c) {
+        const int s = cidx[c] / nn, a = cidx[c] % nn;
+        loc[(size_t)(a * D + i) * n_cells + s] = 0.0;
+      }
+    } else {
+      const double w = split ? v / (double)(c1 - c0) : v;
+      for (int c = c0; c < c1; ++c) {
+        const int s = cidx[c] / nn, a = cidx[c] % nn;
+        loc[(size_t)(a * D + i) * n_cells + s] = w;
+      }
+    }
+  }
+}
+
+// rhs local part: -f on free remaining rows, 0 on corner and fixed rows
+__global__ void k_neg_masked(int64_t n, const double* __restrict__ f, const uint8_t* __restrict__ fixed,
+                             double* __restrict__ out) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fixed[i] ? 0.0 : -f[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// preconditioner setup kernels
+// ---------------------------------------------------------------------------------------------
+// per cell: principal with the largest coefficient, scale c_s = sum_r alpha_r^s, key
+__global__ void k_cell_keys(int n_cells, int n_r, int force_all, const double* __restrict__ alpha,
+                            const int* __restrict__ cls, int n_classes, int* __restrict__ key,
+                            double* __restrict__ cscale) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_cells) return;
+  int best = 0;
+  double c = 1.0;
+  if (force_all) {
+    best = s;
+  } else {
+    double bv = -DBL_MAX, sum = 0;
+    for (int r = 0; r < n_r; ++r) {
+      double a = alpha[(size_t)r * n_cells + s];
+      sum += a;
+      if (a > bv) {
+        bv = a;
+        best = r;
+      }
+    }
+    c = sum > 0 ? sum : (bv > 0 ? bv : 1.0);
+  }
+  key[s] = best * n_classes + cls[s];
+  cscale[s] = c;
+}
+
+// dense local blocks of principal r for key slot k: K_RR (into G, identity on fixed remaining
+// rows), K_RP and K_PP, from the pattern values, masked with the class representative
+template <int D>
+__global__ void k_densify(int n_keys, const int* __restrict__ key_list, int n_classes,
+                          const int* __restrict__ class_rep, int n_cells, int nn, const int* __restrict__ blk_ptr,
+                          const int* __restrict__ blk_col, int64_t nnz, const double* __restrict__ Kp,
+                          const int* __restrict__ rpos, const int* __restrict__ corner_of_node,
+                          const uint8_t* __restrict__ loc_fixed, int n_R, int n_P,
+                          double* __restrict__ G, double* __restrict__ KRP, double* __restrict__ KPP) {
+  const int k = blockIdx.y;
+  const int key = key_list[k];
+  const int r = key / n_classes, cl = key % n_classes;
+  const int rep = class_rep[cl];
+  const double* K = Kp + (size_t)r * nnz;
+  double* g = G + (size_t)k * n_R * n_R;
+  double* krp = KRP + (size_t)k * n_R * n_P;
+  double* kpp = KPP + (size_t)k * n_P * n_P;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
+    const int ca = corner_of_node[a];
+    for (int bi = blk_ptr[a]; bi < blk_ptr[a + 1]; ++bi) {
+      const int b = blk_col[bi];
+      const int cb = corner_of_node[b];
+      for (int i = 0; i < D; ++i) {
+        const int ka = a * D + i;
+        const bool fa = ca < 0 && loc_fixed[(size_t)ka * n_cells + rep];
+        for (int j = 0; j < D; ++j) {
+          const int kb = b * D + j;
+          const bool fb = cb < 0 && loc_fixed[(size_t)kb * n_cells + rep];
+          double v = K[(size_t)bi * D * D + i * D + j];
+          if (fa || fb) v = 0.0;
+          if (ca < 0 && cb < 0) {
+            if (fa && ka == kb) v = 1.0;
+            g[(size_t)rpos[ka] * n_R + rpos[kb]] = v;
+          } else if (ca < 0 && cb >= 0) {
+            krp[(size_t)rpos[ka] * n_P + cb * D + j] = v;
+          } else if (ca >= 0 && cb >= 0) {
+            kpp[(size_t)(ca * D + i) * n_P + cb * D + j] = v;
+          }
+        }
+      }
+    }
+  }
+}
+
+// --- blocked in-place Gauss-Jordan inversion of SPD matrices (batched) -----------------------
+// step with pivot block p = [k0, k0+kw):  Pi = A_pp^{-1};  A_ij -= A_ip Pi A_pj (i,j not in p);
+// A_pj = Pi A_pj;  A_ip = -A_ip Pi;  A_pp = Pi.
+constexpr int GJB = 32;
+
+__global__ void k_gj_pivot(int n, int k0, int kw, double* __restrict__ A, double* __restrict__ Pinv,
+                           double* __restrict__ Cbuf, int* __restrict__ flag) {
+  __shared__ double M[GJB][GJB + 1];
+  const int b = blockIdx.x;
+  double* a = A + (size_t)b * n * n;
+  const int t = threadIdx.x;  // 1024 threads: (i, j)
+  const int i = t / GJB, j = t % GJB;
+  if (i < kw && j < kw) M[i][j] = a[(size_t)(k0 + i) * n + k0 + j];
+  // column panel copy (old values) for the trailing update
+  for (int r = t; r < n * kw; r += blockDim.x) {
+    const int row = r / kw, c = r % kw;
+    Cbuf[((size_t)b * n + row) * GJB + c] = a[(size_t)row * n + k0 + c];
+  }
+  __syncthreads();
+  for (int p = 0; p < kw; ++p) {
+    const double piv = M[p][p];
+    if (t == 0) {
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(flag, 1);
+      else if (piv < 0.0) atomicOr(flag, 2);
+    }
+    const double d = piv != 0.0 ? 1.0 / piv : 0.0;
+    double mij = 0, mip = 0, mpj = 0;
+    if (i < kw && j < kw) {
+      mij = M[i][j];
+      mip = M[i][p];
+      mpj = M[p][j];
+    }
+    __syncthreads();
+    if (i < kw && j < kw) {
+      if (i != p && j != p) M[i][j] = mij - mip * mpj * d;
+      else if (i == p && j != p) M[i][j] = mpj * d;
+      else if (i != p && j == p) M[i][j] = -mip * d;
+      else M[i][j] = d;
+    }
+    __syncthreads();
+  }
+  if (i < kw && j < kw) Pinv[(size_t)b * GJB * GJB + i * GJB + j] = M[i][j];
+}
+
+// Rbuf[b][m][j] = sum_l Pinv[m][l] A[k0+l][j]  (new pivot rows)
+__global__ void k_gj_rows(int n, int k0, int kw, const double* __restrict__ A, const double* __restrict__ Pinv,
+                          double* __restrict__ Rbuf) {
+  const int b = blockIdx.y;
+  const double* a = A + (size_t)b * n * n;
+  const double* P = Pinv + (size_t)b * GJB * GJB;
+  __shared__ double Ps[GJB][GJB];
+  for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) Ps[t / GJB][t % GJB] = (t / GJB < kw && t % GJB < kw) ? P[t] : 0.0;
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double col[GJB];
+#pragma unroll
+  for (int l = 0; l < GJB; ++l) col[l] = l < kw ? a[(size_t)(k0 + l) * n + j] : 0.0;
+  const bool inp = j >= k0 && j < k0 + kw;
+  for (int m = 0; m < kw; ++m) {
+    double v = 0;
+    if (inp) {
+      v = Ps[m][j - k0];
+    } else {
+#pragma unroll
+      for (int l = 0; l < GJB; ++l) v += Ps[m][l] * col[l];
+    }
+    Rbuf[((size_t)b * GJB + m) * n + j] = v;
+  }
+}
+
+// trailing update over 64x64 tiles; every tile reads only Cbuf / Rbuf / Pinv, so tiles are independent
+__global__ void __launch_bounds__(256) k_gj_update(int n, int k0, int kw, double* __restrict__ A,
+                                                   const double* __restrict__ Pinv, const double* __restrict__ Cbuf,
+                                                   const double* __restrict__ Rbuf) {
+  const int b = blockIdx.z;
+  double* a = A + (size_t)b * n * n;
+  const double* C = Cbuf + (size_t)b * n * GJB;
+  const double* R = Rbuf + (size_t)b * GJB * n;
+  const double* P = Pinv + (size_t)b * GJB * GJB;
+  __shared__ double Cs[64][GJB + 1];
+  __shared__ double Rs[GJB][64 + 1];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  for (int t = threadIdx.x; t < 64 * GJB; t += blockDim.x) {
+    const int r = t / GJB, c = t % GJB;
+    const int gi = i0 + r;
+    Cs[r][c] = (gi < n && c < kw) ? C[(size_t)gi * GJB + c] : 0.0;
+  }
+  for (int t = threadIdx.x; t < GJB * 64; t += blockDim.x) {
+    const int r = t / 64, c = t % 64;
+    const int gj = j0 + c;
+    double v = 0.0;
+    if (gj < n && r < kw) v = (gj >= k0 && gj < k0 + kw) ? P[r * GJB + (gj - k0)] : R[(size_t)r * n + gj];
+    Rs[r][c] = v;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int l = 0; l < kw; ++l) {
+    double cv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cv[u] = Cs[ty + 16 * u][l];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) rv[v] = Rs[l][tx + 16 * v];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += cv[u] * rv[v];
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int gi = i0 + ty + 16 * u;
+    if (gi >= n) continue;
+    const bool ip = gi >= k0 && gi < k0 + kw;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int gj = j0 + tx + 16 * v;
+      if (gj >= n) continue;
+      const bool jp = gj >= k0 && gj < k0 + kw;
+      double* dst = a + (size_t)gi * n + gj;
+      if (ip) *dst = jp ? P[(gi - k0) * GJB + (gj - k0)] : R[(size_t)(gi - k0) * n + gj];
+      else if (jp) *dst = -acc[u][v];        // -A_ip Pi   (Rs holds Pi on pivot columns)
+      else *dst -= acc[u][v];                // A_ij - A_ip (Pi A_pj)
+    }
+  }
+}
+
+// Phi = -G K_RP   [k][n_R][n_P]
+__global__ void k_phi(int n_R, int n_P, const double* __restrict__ G, const double* __restrict__ KRP,
+                      double* __restrict__ Phi) {
+  const int k = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_R * n_P) return;
+  const int i = t / n_P, j = t % n_P;
+  const double* g = G + (size_t)k * n_R * n_R + (size_t)i * n_R;
+  const double* b = KRP + (size_t)k * n_R * n_P;
+  double v = 0;
+  for (int l = 0; l < n_R; ++l) v += g[l] * b[(size_t)l * n_P + j];
+  Phi[(size_t)k * n_R * n_P + t] = -v;
+}
+
+// S = K_PP + K_RP^T Phi  (in place on KPP)   [k][n_P][n_P]
+__global__ void k_schur(int n_R, int n_P, const double* __restrict__ KRP, const double* __restrict__ Phi,
+                        double* __restrict__ S) {
+  const int k = blockIdx.x;
+  for (int t = threadIdx.x; t < n_P * n_P; t += blockDim.x) {
+    const int i = t / n_P, j = t % n_P;
+    const double* a = KRP + (size_t)k * n_R * n_P;
+    const double* b = Phi + (size_t)k * n_R * n_P;
+    double v = 0;
+    for (int l = 0; l < n_R; ++l) v += a[(size_t)l * n_P + i] * b[(size_t)l * n_P + j];
+    S[(size_t)k * n_P * n_P + t] += v;
+  }
+}
+
+// coarse matrix entries: sum over contributions c_s S^{slot(s)}[i][j]
+__global__ void k_coarse(int64_t n_ent, int64_t n_primal, int n_P, const int* __restrict__ row,
+                         const int* __restrict__ col, const int* __restrict__ ptr, const int* __restrict__ src,
+                         const int* __restrict__ slot_of_cell, const double* __restrict__ cscale,
+                         const double* __restrict__ S, double* __restrict__ C) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= n_ent) return;
+  double v = 0;
+  for (int c = ptr[e]; c < ptr[e + 1]; ++c) {
+    const int code = src[c];
+    const int s = code / (n_P * n_P), ij = code % (n_P * n_P);
+    v += cscale[s] * S[(size_t)slot_of_cell[s] * n_P * n_P + ij];
+  }
+  C[(size_t)row[e] * n_primal + col[e]] = v;
+}
+
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+// ---------------------------------------------------------------------------------------------
+// K^-rom application kernels
+// ---------------------------------------------------------------------------------------------
+// plain path / many keys: one CTA per cell, y_R = (1/c_s) G^{slot(s)} x_R  (warp per row)
+template <typename TG>
+__global__ void __launch_bounds__(256)
+    k_local_gemv(int n_cells, int n_R, const TG* __restrict__ G, const int* __restrict__ slot,
+                 const double* __restrict__ cscale, const int* __restrict__ rdofs,
+                 const double* __restrict__ X, double* __restrict__ Y) {
+  extern __shared__ double xs[];
+  const int s = blockIdx.x;
+  for (int k = threadIdx.x; k < n_R; k += blockDim.x) xs[k] = X[(size_t)rdofs[k] * n_cells + s];
+  __syncthreads();
+  const TG* g = G + (size_t)slot[s] * n_R * n_R;
+  const double inv = 1.0 / cscale[s];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < n_R; i += nw) {
+    const TG* gi = g + (size_t)i * n_R;
+    double v = 0;
+    for (int k = lane; k < n_R; k += 32) v += (double)gi[k] * xs[k];
+    v = warp_sum(v);
+    if (lane == 0) Y[(size_t)rdofs[i] * n_cells + s] = v * inv;
+  }
+}
+
+// few keys: segmented GEMM over 64 rows x 64 cells of one key, cells in key order (perm)
+template <typename TG>
+__global__ void __launch_bounds__(256)
+    k_local_segmm(int n_cells, int n_R, const TG* __restrict__ G, const int* __restrict__ tile_seg,
+                  const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
+                  const double* __restrict__ cscale, const int* __restrict__ rdofs, const double* __restrict__ X,
+                  double* __restrict__ Y) {
+  const int tile = blockIdx.x;
+  const int k = tile_seg[tile];
+  const int c0 = tile_c0[tile];
+  const int c_end = seg_ptr[k + 1];
+  const int i0 = blockIdx.y * 64;
+  const TG* g = G + (size_t)k * n_R * n_R;
+  __shared__ double Gs[64][33];
+  __shared__ double Xs[32][65];
+  __shared__ int cells[64];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  if (threadIdx.x < 64) {
+    const int c = c0 + threadIdx.x;
+    cells[threadIdx.x] = c < c_end ? perm[c] : -1;
+  }
+  double acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+  for (int l0 = 0; l0 < n_R; l0 += 32) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
+      const int r = t / 32, c = t % 32;
+      const int gi = i0 + r, gl = l0 + c;
+      Gs[r][c] = (gi < n_R && gl < n_R) ? (double)g[(size_t)gi * n_R + gl] : 0.0;
+    }
+    for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+      const int r = t / 64, c = t % 64;
+      const int gl = l0 + r, s = cells[c];
+      Xs[r][c] = (gl < n_R && s >= 0) ? X[(size_t)rdofs[gl] * n_cells + s] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int l = 0; l < 32; ++l) {
+      double gv[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) gv[u] = Gs[ty + 16 * u][l];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) xv[v] = Xs[l][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(gv[u], xv[v], acc[u][v]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int s = cells[tx + 16 * v];
+    if (s < 0) continue;
+    const double inv = 1.0 / cscale[s];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int gi = i0 + ty + 16 * u;
+      if (gi < n_R) Y[(size_t)rdofs[gi] * n_cells + s] = acc[u][v] * inv;
+    }
+  }
+}
+
+// tP at the corner rows of a local buffer:  buf[pdof_j, s] = sum_i Phi^{slot(s)}[i][j] x_R^s[i]
+__global__ void k_phi_t(int n_cells, int n_R, int n_P, const double* __restrict__ Phi, const int* __restrict__ slot,
+                        const int* __restrict__ rdofs, const int* __restrict__ pdofs, const double* __restrict__ X,
+                        double* __restrict__ buf) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (s >= n_cells) return;
+  const double* ph = Phi + (size_t)slot[s] * n_R * n_P;
+  double v = 0;
+  for (int i = 0; i < n_R; ++i) v += ph[(size_t)i * n_P + j] * X[(size_t)rdofs[i] * n_cells + s];
+  buf[(size_t)pdofs[j] * n_cells + s] = v;
+}
+
+// Y_R^s += Phi^{slot(s)} xP(corners of s)
+__global__ void k_phi_n(int n_cells, int n_R, int n_P, const double* __restrict__ Phi, const int* __restrict__ slot,
+                        const int* __restrict__ rdofs, const int* __restrict__ pidx, const double* __restrict__ xP,
+                        const uint8_t* __restrict__ fixed, double* __restrict__ Y) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (s >= n_cells) return;
+  const double* ph = Phi + (size_t)slot[s] * n_R * n_P + (size_t)i * n_P;
+  double v = 0;
+  for (int j = 0; j < n_P; ++j) {
+    const int p = pidx[(size_t)s * n_P + j];
+    if (p >= 0) v += ph[j] * xP[p];
+  }
+  const size_t e = (size_t)rdofs[i] * n_cells + s;
+  Y[e] = fixed[e] ? 0.0 : Y[e] + v;
+}
+
+// y = A x for a dense row-major matrix (warp per row)
+__global__ void k_gemv(int64_t n, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  const double* a = A + (size_t)row * n;
+  double v = 0;
+  for (int64_t k = lane; k < n; k += 32) v += a[k] * x[k];
+  v = warp_sum(v);
+  if (lane == 0) y[row] = v;
+}
+
+// FGMRES small dense work on one thread: Hessenberg column j (in Hh[(m+1) x m], column major)
+// after the Arnoldi step; Givens rotations in small[0..m) cs, [m..2m) sn, g in [2m..3m+1)
+__global__ void k_givens(int j, int m, double* __restrict__ H, double* __restrict__ small,
+                         const double* __restrict__ hcol, const double* __restrict__ nrm2, double* __restrict__ est) {
+  double* cs = small;
+  double* sn = small + m;
+  double* g = small + 2 * m;
+  double* col = H + (size_t)j * (m + 1);
+  for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+  col[j + 1] = sqrt(nrm2[0]);
+  for (int i = 0; i < j; ++i) {
+    const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+    col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+    col[i] = t;
+  }
+  const double a = col[j], b = col[j + 1];
+  const double r = hypot(a, b);
+  cs[j] = r > 0 ? a / r : 1.0;
+  sn[j] = r > 0 ? b / r : 0.0;
+  col[j] = r;
+  col[j + 1] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  est[0] = fabs(g[j + 1]);
+}
+
+__global__ void k_gmres_init(int m, double* __restrict__ small, const double* __restrict__ nrm2) {
+  for (int i = 0; i < 3 * m + 1; ++i) small[i] = 0.0;
+  small[2 * m] = sqrt(nrm2[0]);
+}
+
+// back substitution H y = g for the first k columns; y written to out[0..k)
+__global__ void k_gmres_solve(int k, int m, const double* __restrict__ H, const double* __restrict__ small,
+                              double* __restrict__ y) {
+  const double* g = small + 2 * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double v = g[i];
+    for (int l = i + 1; l < k; ++l) v -= H[(size_t)l * (m + 1) + i] * y[l];
+    y[i] = v / H[(size_t)i * (m + 1) + i];
+  }
+}
+
+int red_blocks(int64_t n) { return (int)std::min<int64_t>(kRed, std::max<int64_t>(1, (n + 255) / 256)); }
+int ew_blocks(lat_ctx* h, int64_t n) {
+  return (int)std::min<int64_t>((int64_t)h->n_sm * 8, std::max<int64_t>(1, (n + 255) / 256));
+}
+
+// device dot -> out[0] (no host sync)
+void dev_dot(lat_ctx* h, int64_t n, const double* a, const double* b, double* out) {
+  const int nb = red_blocks(n);
+  k_dot_part<<<nb, 256, 0, h->stream>>>(n, a, b, h->red_part.p + 1024);
+  k_sum_part<<<1, 512, 0, h->stream>>>(nb, h->red_part.p + 1024, out);
+}
+
+struct SolverTmp {
+  double *a, *b, *c;
+};
+
+// ---------------------------------------------------------------------------------------------
+// preconditioner setup
+// ---------------------------------------------------------------------------------------------
+void gj_invert(lat_ctx* h, double* A, int n, int batch) {
+  DBuf<double> Pinv, Cbuf, Rbuf;
+  Pinv.ensure((size_t)batch * GJB * GJB);
+  Cbuf.ensure((size_t)batch * n * GJB);
+  Rbuf.ensure((size_t)batch * GJB * n);
+  for (int k0 = 0; k0 < n; k0 += GJB) {
+    const int kw = std::min(GJB, n - k0);
+    k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p);
+    k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, k0, kw, A, Pinv.p, Rbuf.p);
+    k_gj_update<<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(n, k0, kw, A, Pinv.p,
+                                                                                   Cbuf.p, Rbuf.p);
+    LAT_CHECK_LAUNCH();
+  }
+  LAT_CUDA(cudaStreamSynchronize(h->stream));
+  Pinv.release();
+  Cbuf.release();
+  Rbuf.release();
+}
+
+}  // namespace
+
+void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
+  (void)o;
+  LAT_REQUIRE(h->n_r > 0, LAT_EINVAL, "select principal cells first");
+  const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
+  h->flag.ensure(4);
+  h->red_part.ensure(4096);
+  LAT_CUDA(cudaMemsetAsync(h->flag.p, 0, 4 * sizeof(int), h->stream));
+  // keys and scales
+  h->key_of_cell.ensure(ns);
+  h->c_cell.ensure(ns);
+  k_cell_keys<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, h->n_r, h->force_all ? 1 : 0, h->alpha.p,
+                                                      h->cell_class.p, h->n_classes, h->key_of_cell.p, h->c_cell.p);
+  LAT_CHECK_LAUNCH();
+  std::vector<int> keys(ns);
+  LAT_CUDA(cudaMemcpyAsync(keys.data(), h->key_of_cell.p, ns * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LAT_CUDA(cudaStreamSynchronize(h->stream));
+  // segments: cells grouped by key (stable, cell order inside a key)
+  std::vector<int> uniq(keys);
+  std::sort(uniq.begin(), uniq.end());
+  uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+  const int nk = (int)uniq.size();
+  const int n_key_space = h->n_r * h->n_classes;
+  std::vector<int> slot(n_key_space, -1);
+  for (int k = 0; k < nk; ++k) slot[uniq[k]] = k;
+  std::vector<int> cnt(nk + 1, 0), perm(ns), slot_cell(ns);
+  for (int s = 0; s < ns; ++s) {
+    slot_cell[s] = slot[keys[s]];
+    cnt[slot_cell[s] + 1]++;
+  }
+  for (int k = 0; k < nk; ++k) cnt[k + 1] += cnt[k];
+  std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+  for (int s = 0; s < ns; ++s) perm[fill[slot_cell[s]]++] = s;
+  std::vector<int> tseg, tc0;
+  for (int k = 0; k < nk; ++k)
+    for (int c = cnt[k]; c < cnt[k + 1]; c += 64) {
+      tseg.push_back(k);
+      tc0.push_back(c);
+    }
+  h->n_keys = nk;
+  h->key_list.upload(uniq, h->stream);
+  h->perm.upload(perm, h->stream);
+  h->seg_ptr.upload(cnt, h->stream);
+  h->tile_seg.upload(tseg, h->stream);
+  h->tile_c0.upload(tc0, h->stream);
+  h->max_tiles = (int)tseg.size();
+  h->key_slot.upload(slot_cell, h->stream);  // slot of each cell
+  // dense local blocks
+  const size_t gsz = (size_t)nk * nR * nR;
+  h->G.ensure(gsz);
+  h->KRP.ensure((size_t)nk * nR * nP);
+  h->Sloc.ensure((size_t)nk * nP * nP);
+  h->Phi.ensure((size_t)nk * nR * nP);
+  LAT_CUDA(cudaMemsetAsync(h->G.p, 0, gsz * sizeof(double), h->stream));
+  LAT_CUDA(cudaMemsetAsync(h->KRP.p, 0, (size_t)nk * nR * nP * sizeof(double), h->stream));
+  LAT_CUDA(cudaMemsetAsync(h->Sloc.p, 0, (size_t)nk * nP * nP * sizeof(double), h->stream));
+  DBuf<int> crep;
+  crep.upload(h->class_rep, h->stream);
+  {
+    dim3 grid(div_up(h->n_nodes_cell, 128), nk);
+    if (h->dim == 2)
+      k_densify<2><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
+          h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
+          nR, nP, h->G.p, h->KRP.p, h->Sloc.p);
+    else
+      k_densify<3><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
+          h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
+          nR, nP, h->G.p, h->KRP.p, h->Sloc.p);
+    LAT_CHECK_LAUNCH();
+  }
+  gj_invert(h, h->G.p, nR, nk);
+  k_phi<<<dim3(div_up(nR * nP, 128), nk), 128, 0, h->stream>>>(nR, nP, h->G.p, h->KRP.p, h->Phi.p);
+  k_schur<<<nk, 64, 0, h->stream>>>(nR, nP, h->KRP.p, h->Phi.p, h->Sloc.p);
+  LAT_CHECK_LAUNCH();
+  // coarse matrix, FP64, explicit inverse
+  const int64_t np = h->n_primal;
+  if (np > 0) {
+    h->CoarseInv.ensure((size_t)np * np);
+    LAT_CUDA(cudaMemsetAsync(h->CoarseInv.p, 0, (size_t)np * np * sizeof(double), h->stream));
+    const int64_t n_ent = (int64_t)h->coarse_row.n;
+    k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p, h->coarse_col.p,
+        h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p);
+    LAT_CHECK_LAUNCH();
+    gj_invert(h, h->CoarseInv.p, (int)np, 1);
+  }
+  int fl = 0;
+  LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LAT_CUDA(cudaStreamSynchronize(h->stream));
+  crep.release();
+  LAT_REQUIRE(!(fl & 1), LAT_EINDEFINITE, "a local remaining-DOF matrix or the coarse matrix is singular");
+  h->indefinite = (fl & 2) != 0;
+  if (h->prec != LAT_FP64) {
+    h->G32.ensure(gsz);
+    k_d2f<<<ew_blocks(h, gsz), 256, 0, h->stream>>>(gsz, h->G.p, h->G32.p);
+    LAT_CHECK_LAUNCH();
+  }
+  // temporaries
+  for (int i = 0; i < 6; ++i) h->kv_tmp[i].ensure(h->n_krylov);
+  h->gP.ensure(std::max<int64_t>(np, 1));
+  h->xP.ensure(std::max<int64_t>(np, 1));
+}
+
+namespace {
+
+double* loc_of(lat_ctx* h, double* v) { return v; }
+double* pr_of(lat_ctx* h, double* v) { return v + (size_t)h->n_loc * h->n_cells; }
+double* la_of(lat_ctx* h, double* v) { return v + (size_t)h->n_loc * h->n_cells + h->n_primal; }
+const double* pr_of(lat_ctx* h, const double* v) { return v + (size_t)h->n_loc * h->n_cells; }
+const double* la_of(lat_ctx* h, const double* v) { return v + (size_t)h->n_loc * h->n_cells + h->n_primal; }
+
+// w_u = K~ v_u (+ B^T v_l when with_bt), w_l = B v_u  (saddle-point operator)
+void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda) {
+  const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
+  const double* vP = pr_of(h, v);
+  // the Krylov operator stays FP64 in every mode: FGMRES then solves the FP64 system to its
+  // tolerance, while the mixed modes lower the precision of the preconditioner only
+  run_apply(h, v, w, 0, vP, true);
+  // primal rows -> assembled primal part, then clear corner rows
+  if (h->n_primal)
+    k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
+        h->p_copy.p, w, pr_of(h, w), 0);
+  k_zero_rows<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->n_P, h->pdofs.p, w);
+  if (h->n_lambda) {
+    if (with_lambda)
+      k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+          h->dual_l2.p, nullptr, la_of(h, v), 1.0, w);
+    k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, v, 1.0,
+                                                              la_of(h, w), 0);
+  }
+  LAT_CHECK_LAUNCH();
+}
+
+// w_u = K^-rom v_u  (local part and primal part; multiplier part untouched)
+void kinv(lat_ctx* h, const double* v, double* w) {
+  const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
+  const int64_t nloc = (int64_t)h->n_loc * ns;
+  double* wl = loc_of(h, w);
+  LAT_CUDA(cudaMemsetAsync(wl, 0, nloc * sizeof(double), h->stream));
+  // y_R = G~ v_R
+  const bool gemv = (int64_t)h->n_keys * 8 > ns;
+  const bool lo = h->prec != LAT_FP64;
+  if (gemv) {
+    const size_t shm = (size_t)nR * sizeof(double);
+    if (lo) {
+      LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nR, h->G32.p, h->key_slot.p, h->c_cell.p, h->rdofs.p, v, wl);
+    } else {
+      LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, h->G.p, h->key_slot.p, h->c_cell.p, h->rdofs.p, v, wl);
+    }
+  } else {
+    dim3 grid(h->max_tiles, div_up(nR, 64));
+    if (lo)
+      k_local_segmm<float><<<grid, 256, 0, h->stream>>>(ns, nR, h->G32.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, v, wl);
+    else
+      k_local_segmm<double><<<grid, 256, 0, h->stream>>>(ns, nR, h->G.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, v, wl);
+  }
+  LAT_CHECK_LAUNCH();
+  if (h->n_primal) {
+    // g_P = v_P + sum_s A_P^T Phi^T v_R   (corner rows of wl are free scratch here)
+    k_phi_t<<<dim3(div_up(ns, 128), nP), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
+                                                              h->pdofs.p, v, wl);
+    LAT_CUDA(cudaMemcpyAsync(h->gP.p, pr_of(h, v), h->n_primal * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
+        h->p_copy.p, wl, h->gP.p, 1);
+    k_gemv<<<div_up(h->n_primal * 32, 256), 256, 0, h->stream>>>(h->n_primal, h->CoarseInv.p, h->gP.p, pr_of(h, w));
+    k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl);
+    k_phi_n<<<dim3(div_up(ns, 128), nR), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
+                                                               h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl);
+    LAT_CHECK_LAUNCH();
+  }
+}
+
+// S_op p = B K^-rom B^T p (multiplier vectors); uses tmp (saddle sized) as scratch
+void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
+  const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
+  LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
+  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, nullptr, p, 1.0, t1);
+  LAT_CHECK_LAUNCH();
+  kinv(h, t1, t2);
+  k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, 1.0, q, 0);
+  LAT_CHECK_LAUNCH();
+}
+
+// lumped preconditioner z = B_D K~_dd B_D^T r
+void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2, double* wloc) {
+  const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
+  LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
+  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, h->dual_scale.p, r, 1.0, t1);
+  LAT_CHECK_LAUNCH();
+  // K~ on the dual-only local vector (corners zero: primal part of t1 is zero)
+  if (h->prec == LAT_FP64) {
+    run_apply(h, t1, t2, 0, pr_of(h, t1), true);
+  } else {
+    h->x32.ensure(nloc);
+    h->y32.ensure(nloc);
+    k_d2f<<<ew_blocks(h, nloc), 256, 0, h->stream>>>(nloc, t1, h->x32.p);
+    run_apply(h, h->x32.p, h->y32.p, 1, pr_of(h, t1), true);
+    run_f2d(h, nloc, h->y32.p, t2);
+  }
+  k_jump_scaled<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, wloc, z);
+  LAT_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void run_feti_operator(lat_ctx* h, const double* v, double* w) { feti_operator(h, v, w, true); }
+
+void run_kinv(lat_ctx* h, const double* v, double* w) {
+  kinv(h, v, w);
+  if (h->n_lambda)
+    LAT_CUDA(cudaMemcpyAsync(la_of(h, w), la_of(h, v), h->n_lambda * sizeof(double), cudaMemcpyDeviceToDevice,
+                             h->stream));
+}
+
+void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters) {
+  const int64_t L = h->n_lambda;
+  double* t = h->kv_tmp[2].p;   // K^-rom v_u, later v_u - B^T z
+  double* t1 = h->kv_tmp[3].p;
+  double* t2 = h->kv_tmp[4].p;
+  double* pv = h->kv_tmp[5].p;  // multiplier work vectors carved from one saddle-sized buffer
+  if (L == 0) {
+    kinv(h, v, w);
+    return;
+  }
+  kinv(h, v, t);
+  double* y = pv;            // rhs of the interface solve, then residual r
+  double* x = pv + L;        // solution
+  double* z = pv + 2 * L;
+  double* p = pv + 3 * L;
+  double* q = pv + 4 * L;
+  double* wloc = h->kv_tmp[1].p;  // dual weights (1/multiplicity) as a dense local array
+  LAT_REQUIRE(5 * L <= h->n_krylov, LAT_EINVAL, "multiplier work space too small");
+  const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
+  LAT_CUDA(cudaMemsetAsync(wloc, 0, nloc * sizeof(double), h->stream));
+  k_fill_dual_weights<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_scale.p, wloc);
+  // y = v_l - B t
+  LAT_CUDA(cudaMemcpyAsync(y, la_of(h, v), L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  k_jump<<<div_up(L, 256), 256, 0, h->stream>>>(L, h->lam_p.p, h->lam_m.p, t, -1.0, y, 1);
+  LAT_CHECK_LAUNCH();
+  // PCG on S x = y from x = 0
+  LAT_CUDA(cudaMemsetAsync(x, 0, L * sizeof(double), h->stream));
+  double* sc = h->red_part.p + 3000;  // see k_pcg_alpha
+  if (pcg_iters > 0) {
+    LAT_CUDA(cudaMemsetAsync(sc, 0, 8 * sizeof(double), h->stream));
+    dual_precond(h, y, z, t1, t2, wloc);
+    LAT_CUDA(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    dev_dot(h, L, y, z, sc);
+    const int nb = ew_blocks(h, L);
+    for (int it = 0; it < pcg_iters; ++it) {
+      dual_op(h, p, q, t1, t2);
+      dev_dot(h, L, p, q, sc + 1);
+      k_pcg_alpha<<<1, 1, 0, h->stream>>>(sc);
+      k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, 1.0, p, x);
+      if (it + 1 == pcg_iters) break;
+      k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, -1.0, q, y);
+      dual_precond(h, y, z, t1, t2, wloc);
+      dev_dot(h, L, y, z, sc + 2);
+      k_pcg_beta<<<1, 1, 0, h->stream>>>(sc);
+      k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p);
+      LAT_CHECK_LAUNCH();
+    }
+  }
+  // z_l = -x ;  w_u = K^-rom (v_u - B^T z_l) = K^-rom (v_u + B^T x)
+  LAT_CUDA(cudaMemcpyAsync(t, v, (nloc + h->n_primal) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, nullptr, x, 1.0, t);
+  LAT_CHECK_LAUNCH();
+  kinv(h, t, w);
+  k_axpby<<<ew_blocks(h, L), 256, 0, h->stream>>>(L, -1.0, x, 0.0, la_of(h, w));
+  LAT_CHECK_LAUNCH();
+}
+
+// right-preconditioned restarted FGMRES from x (in/out); returns iterations, *rel = final estimate
+int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o, double* rel_out) {
+  const int64_t n = h->n_krylov;
+  const int m = std::max(2, o->krylov_restart);
+  h->V.ensure((size_t)(m + 1) * n);
+  h->Zk.ensure((size_t)m * n);
+  h->Hh.ensure((size_t)(m + 1) * m + 4 * (m + 1));
+  h->gmres_small.ensure(3 * m + 8);
+  const int nb = red_blocks(n);
+  h->dots_part.ensure((size_t)(m + 1) * nb);
+  double* sc = h->red_part.p + 3100;  // [0] nrm2, [1] est, [2..] h column, y
+  double* hcol = h->red_part.p + 3200;
+  double* h2 = h->red_part.p + 3400;
+  double* yv = h->red_part.p + 3600;
+  LAT_REQUIRE(m <= 190, LAT_EINVAL, "krylov_restart too large (max 190)");
+  double* w = h->kv_tmp[0].p;
+  const int eb = ew_blocks(h, n);
+  double* hp = h->h_pinned;
+  // ||b||
+  dev_dot(h, n, b, b, sc);
+  LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LAT_CUDA(cudaStreamSynchronize(h->stream));
+  const double bnorm = std::sqrt(hp[0]);
+  if (bnorm == 0.0) {
+    LAT_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), h->stream));
+    if (rel_out) *rel_out = 0;
+    return 0;
+  }
+  int total = 0;
+  double rel = 1.0;
+  while (total < o->krylov_max_it) {
+    // r = b - A x
+    feti_operator(h, x, w, true);
+    k_axpby<<<eb, 256, 0, h->stream>>>(n, 1.0, b, -1.0, w);
+    dev_dot(h, n, w, w, sc);
+    LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    rel = std::sqrt(hp[0]) / bnorm;
+    if (rel <= o->krylov_rtol) break;
+    k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p);
+    k_gmres_init<<<1, 1, 0, h->stream>>>(m, h->gmres_small.p, sc);
+    int j = 0;
+    for (; j < m && total < o->krylov_max_it; ++j, ++total) {
+      double* vj = h->V.p + (size_t)j * n;
+      double* zj = h->Zk.p + (size_t)j * n;
+      run_block_precond(h, vj, zj, o->pcg_iters);
+      feti_operator(h, zj, w, true);
+      // CGS with one re-orthogonalisation
+      for (int pass = 0; pass < 2; ++pass) {
+        k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, h->V.p, w, h->dots_part.p);
+        k_multidot_final<<<j + 1, 256, 0, h->stream>>>(nb, h->dots_part.p, pass == 0 ? hcol : h2);
+        k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j + 1, h->V.p, pass == 0 ? hcol : h2, -1.0, w);
+      }
+      k_axpby<<<1, 256, 0, h->stream>>>(j + 1, 1.0, h2, 1.0, hcol);
+      dev_dot(h, n, w, w, sc);
+      k_givens<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, hcol, sc, sc + 1);
+      k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p + (size_t)(j + 1) * n);
+      LAT_CHECK_LAUNCH();
+      LAT_CUDA(cudaMemcpyAsync(hp, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LAT_CUDA(cudaStreamSynchronize(h->stream));
+      rel = hp[1] / bnorm;
+      if (rel <= o->krylov_rtol || !(hp[0] > 0.0)) {
+        ++j;
+        ++total;
+        break;
+      }
+    }
+    // x += Z y
+    k_gmres_solve<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, yv);
+    k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j, h->Zk.p, yv, 1.0, x);
+    LAT_CHECK_LAUNCH();
+    if (rel <= o->krylov_rtol) break;
+  }
+  if (rel_out) *rel_out = rel;
+  return total;
+}
+
+void run_feti_to_global(lat_ctx* h, const double* v, double* u) {
+  k_to_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
+      h->n_cells, h->n_P, h->copy_ptr.p, h->copy_idx.p, h->corner_of_node.p, h->pidx.p, h->dof_fixed.p,
+      v, pr_of(h, v), u);
+  LAT_CHECK_LAUNCH();
+}
+
+void run_feti_from_global(lat_ctx* h, const double* u, double* v, bool split) {
+  LAT_CUDA(cudaMemsetAsync(v, 0, h->n_krylov * sizeof(double), h->stream));
+  k_from_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
+      h->n_cells, h->n_P, h->copy_ptr.p, h->copy_idx.p, h->corner_of_node.p, h->pidx.p, h->dof_fixed.p,
+      u, split ? 1 : 0, v, pr_of(h, v));
+  LAT_CHECK_LAUNCH();
+}
+
+void run_axpy(lat_ctx* h, int64_t n, double a, const double* x, double* y) {
+  k_axpby<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, a, x, 1.0, y);
+  LAT_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Newton, adjoint and the remaining entry points
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+void check_opts(const lat_newton_opts* o) {
+  LAT_REQUIRE(o, LAT_EINVAL, "options required");
+  LAT_REQUIRE(o->krylov_restart >= 2 && o->krylov_restart <= 190, LAT_EINVAL, "krylov_restart in [2, 190]");
+  LAT_REQUIRE(o->krylov_max_it >= 1 && o->newton_max_it >= 1 && o->armijo_max_m >= 0 && o->pcg_iters >= 0,
+              LAT_EINVAL, "iteration caps must be positive");
+  LAT_REQUIRE(o->force_all || o->max_nr >= 1, LAT_EINVAL, "max_nr must be >= 1");
+}
+
+// FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
+// remaining DOF, assembled on the free primal DOFs, zero multipliers.  Any split that sums to -r
+// gives the same du; the even split keeps ||rhs|| ~ ||r_F|| (the raw per-cell forces do not
+// cancel at interfaces and would make the relative Krylov tolerance an absolute floor).
+void newton_rhs(lat_ctx* h, const double* r_glob, double* b) {
+  run_feti_from_global(h, r_glob, b, true);
+  k_axpby<<<ew_blocks(h, h->n_krylov), 256, 0, h->stream>>>(h->n_krylov, 0.0, b, -1.0, b);
+  LAT_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
+  if (!h || !o) return LAT_EINVAL;
+  o->eps = h->dim == 2 ? 3e-4 : 5e-3;
+  o->max_nr = 256;
+  o->force_all = 0;
+  o->newton_rtol = 1e-8;
+  o->newton_max_it = 30;
+  o->krylov_rtol = h->prec == LAT_FP64 ? 1e-10 : 1e-6;
+  o->krylov_max_it = 600;
+  o->krylov_restart = 60;
+  o->pcg_iters = 5;
+  o->armijo_max_m = 30;
+  return LAT_OK;
+}
+
+extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iterations, const lat_newton_opts* o,
+                                  lat_newton_report* rep) {
+  if (!h || !u) return LAT_EINVAL;
+  lat_newton_report R{};
+  lat_status st = guard(h, [&] {
+    check_opts(o);
+    const int64_t nd = h->n_dof;
+    h->f_cells.ensure((size_t)h->n_loc * h->n_cells);
+    h->r_glob.ensure(nd);
+    DBuf<double> du, ut;
+    du.ensure(nd);
+    ut.ensure(nd);
+    double t0 = now_ms();
+    bool neg = false;
+    run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
+    LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 at the initial guess");
+    double rn = run_norm_free(h, h->r_glob.p);
+    double floor = 1e-12 * run_norm_all(h, h->r_glob.p);
+    R.t_residual_ms += now_ms() - t0;
+    R.r0_norm = rn;
+    const double r0 = rn;
+    const int cap = max_iterations > 0 ? max_iterations : o->newton_max_it;
+    int it = 0;
+    while (!(rn <= o->newton_rtol * r0 || rn <= floor) && it < cap) {
+      double ta = now_ms();
+      select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
+      double tb = now_ms();
+      R.t_select_ms += tb - ta;
+      run_prepare_solver(h, o);
+      double tc = now_ms();
+      R.t_setup_ms += tc - tb;
+      R.n_r_last = h->n_r;
+      DBuf<double> rhs, sol;
+      rhs.ensure(h->n_krylov);
+      sol.ensure(h->n_krylov);
+      newton_rhs(h, h->r_glob.p, rhs.p);
+      LAT_CUDA(cudaMemsetAsync(sol.p, 0, h->n_krylov * sizeof(double), h->stream));
+      double rel = 0;
+      R.krylov_its_total += run_fgmres(h, rhs.p, sol.p, o, &rel);
+      run_feti_to_global(h, sol.p, du.p);
+      double td = now_ms();
+      R.t_krylov_ms += td - tc;
+      // Armijo backtracking (Section 2.2.5)
+      bool accepted = false;
+      double step = 1.0, rt = 0;
+      int mm = 0;
+      for (; mm <= o->armijo_max_m; ++mm, step *= 0.5) {
+        LAT_CUDA(cudaMemcpyAsync(ut.p, u, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        run_axpy(h, nd, step, du.p, ut.p);
+        bool ng = false;
+        run_residual(h, ut.p, h->f_cells.p, h->r_glob.p, nullptr, &ng);
+        if (ng) continue;
+        rt = run_norm_free(h, h->r_glob.p);
+        if (rt <= (1.0 - 1e-4 * step) * rn) {
+          accepted = true;
+          break;
+        }
+      }
+      R.t_linesearch_ms += now_ms() - td;
+      R.armijo_m_max = std::max(R.armijo_m_max, mm);
+      if (h->verbose)
+        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d indef=%d krylov=%d (rel %.1e) m=%d%s\n",
+                     it, rn, rn / r0, h->n_r, h->n_keys, (int)h->indefinite, R.krylov_its_total, rel, mm,
+                     accepted ? "" : " REJECTED");
+      if (!accepted) {
+        // leave u and the residual buffers consistent with u
+        run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
+        R.r_norm = rn;
+        R.iterations = it;
+        throw LatError{LAT_ENOT_CONVERGED, "Armijo line search found no acceptable step"};
+      }
+      LAT_CUDA(cudaMemcpyAsync(u, ut.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      rn = rt;
+      floor = 1e-12 * run_norm_all(h, h->r_glob.p);
+      ++it;
+      rhs.release();
+      sol.release();
+    }
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    R.iterations = it;
+    R.r_norm = rn;
+    R.converged = (rn <= o->newton_rtol * r0 || rn <= floor) ? 1 : 0;
+    du.release();
+    ut.release();
+  });
+  if (rep) *rep = R;
+  return st;
+}
+
+extern "C" lat_status lattice_prepare_solver(lat_handle h, const double* u, const lat_newton_opts* o) {
+  if (!h || !u) return LAT_EINVAL;
+  return guard(h, [&] {
+    check_opts(o);
+    (void)u;
+    run_prepare_solver(h, o);
+  });
+}
+
+extern "C" lat_status tangent_solve(lat_handle h, const double* rhs, double* x, const lat_newton_opts* o,
+                                    int32_t* iters, double* rel) {
+  if (!h || !rhs || !x) return LAT_EINVAL;
+  return guard(h, [&] {
+    check_opts(o);
+    LAT_REQUIRE(h->n_keys > 0, LAT_EINVAL, "call lattice_prepare_solver first");
+    DBuf<double> b, sol;
+    b.ensure(h->n_krylov);
+    sol.ensure(h->n_krylov);
+    run_feti_from_global(h, rhs, b.p, true);
+    LAT_CUDA(cudaMemsetAsync(sol.p, 0, h->n_krylov * sizeof(double), h->stream));
+    double r = 0;
+    const int it = run_fgmres(h, b.p, sol.p, o, &r);
+    run_feti_to_global(h, sol.p, x);
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    if (iters) *iters = it;
+    if (rel) *rel = r;
+  });
+}
+
+extern "C" lat_status feti_apply(lat_handle h, int32_t mode, const double* v, double* w) {
+  if (!h || !v || !w) return LAT_EINVAL;
+  return guard(h, [&] {
+    LAT_REQUIRE(h->n_keys > 0, LAT_EINVAL, "call lattice_prepare_solver first");
+    if (mode == 0) run_feti_operator(h, v, w);
+    else if (mode == 1) run_kinv(h, v, w);
+    else if (mode == 2) run_block_precond(h, v, w, 5);
+    else throw LatError{LAT_EINVAL, "mode must be 0, 1 or 2"};
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+extern "C" lat_status feti_to_global(lat_handle h, const double* v, double* u) {
+  if (!h || !v || !u) return LAT_EINVAL;
+  return guard(h, [&] { run_feti_to_global(h, v, u); });
+}
+
+extern "C" lat_status feti_from_global(lat_handle h, const double* u, double* v) {
+  if (!h || !v || !u) return LAT_EINVAL;
+  return guard(h, [&] { run_feti_from_global(h, u, v, false); });
+}
+
+extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_newton_opts* o, double* grad,
+                                       double* J, lat_newton_report* rep) {
+  if (!h || !u || !grad) return LAT_EINVAL;
+  lat_newton_report R{};
+  lat_status st = guard(h, [&] {
+    check_opts(o);
+    const int64_t nd = h->n_dof;
+    h->f_cells.ensure((size_t)h->n_loc * h->n_cells);
+    h->r_glob.ensure(nd);
+    bool neg = false;
+    run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
+    LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 at the adjoint state");
+    if (J) *J = run_dot_fixed(h, u, h->r_glob.p);
+    DBuf<double> vD, bF, lam, d, y, rhs, sol, del;
+    for (auto* p : {&vD, &bF, &lam, &d, &y, &del}) p->ensure(nd);
+    rhs.ensure(h->n_krylov);
+    sol.ensure(h->n_krylov);
+    // v_D = u on the Dirichlet DOFs, 0 elsewhere;  b_F = (K v_D)_F = K_FD u_D
+    run_mask(h, u, vD.p, 1);
+    run_tangent_apply_exact(h, u, vD.p, y.p);
+    run_mask(h, y.p, bF.p, 0);
+    const double bnorm = run_norm_free(h, bF.p);
+    LAT_CUDA(cudaMemsetAsync(lam.p, 0, nd * sizeof(double), h->stream));
+    LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
+    run_prepare_solver(h, o);
+    R.n_r_last = h->n_r;
+    double dn = bnorm;
+    R.r0_norm = bnorm;
+    int it = 0;
+    const double tol = std::max(o->newton_rtol * 1e-2, 1e-12);
+    while (bnorm > 0 && dn > tol * bnorm && it < o->newton_max_it) {
+      run_feti_from_global(h, d.p, rhs.p, true);
+      LAT_CUDA(cudaMemsetAsync(sol.p, 0, h->n_krylov * sizeof(double), h->stream));
+      double rel = 0;
+      R.krylov_its_total += run_fgmres(h, rhs.p, sol.p, o, &rel);
+      run_feti_to_global(h, sol.p, del.p);
+      run_axpy(h, nd, 1.0, del.p, lam.p);
+      // defect d = b_F - (K lambda)_F with the exact tangent action
+      run_tangent_apply_exact(h, u, lam.p, y.p);
+      LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      run_axpy(h, nd, -1.0, y.p, d.p);
+      run_mask(h, d.p, d.p, 0);
+      dn = run_norm_free(h, d.p);
+      ++it;
+    }
+    R.iterations = it;
+    R.r_norm = dn;
+    R.converged = (bnorm == 0 || dn <= tol * bnorm) ? 1 : 0;
+    // w = -lambda on free DOFs, u_D on Dirichlet DOFs
+    run_adjoint_w(h, lam.p, u, y.p);
+    run_grad_mu(h, u, y.p, grad);
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto* p : {&vD, &bF, &lam, &d, &y, &rhs, &sol, &del}) p->release();
+    LAT_REQUIRE(R.converged, LAT_ENOT_CONVERGED, "adjoint defect correction did not converge");
+  });
+  if (rep) *rep = R;
+  return st;
+}
+
+// --- small helpers used above ----------------------------------------------------------------
+namespace {
+__global__ void k_f2d(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+__global__ void k_mask(int64_t n, const double* __restrict__ x, const uint8_t* __restrict__ fixed, int keep_fixed,
+                       double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = ((fixed[i] != 0) == (keep_fixed != 0)) ? x[i] : 0.0;
+}
+__global__ void k_adj_w(int64_t n, const double* __restrict__ lam, const double* __restrict__ u,
+                        const uint8_t* __restrict__ fixed, double* __restrict__ w) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) w[i] = fixed[i] ? u[i] : -lam[i];
+}
+}  // namespace
+
+void run_f2d(lat_ctx* h, int64_t n, const float* x, double* y) {
+  k_f2d<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, x, y);
+  LAT_CHECK_LAUNCH();
+}
+void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed) {
+  k_mask<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, x, h->dof_fixed.p, keep_fixed, y);
+  LAT_CHECK_LAUNCH();
+}
+void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w) {
+  k_adj_w<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, lam, u, h->dof_fixed.p, w);
+  LAT_CHECK_LAUNCH();
+}

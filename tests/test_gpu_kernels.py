@@ -1,0 +1,213 @@
+"""GPU parity of the per-cell kernels, the greedy selection and the reduced tangent action.
+
+Every comparison is element by element against the FP64 CPU oracle on the same seeded inputs.
+Tolerances: FP64 paths agree to rounding (relative 1e-11 of the largest entry: the GPU sums in a
+different order than numpy); the FP32 action to 2e-6 relative (24-bit mantissa, sums of a few
+hundred terms).  Integer results (principal sets) must be identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+import latgen
+from oracle import cell as OC
+from oracle import greedy as OG
+from oracle import newton as ON
+from oracle import rom as OR
+from oracle.assembly import Problem
+
+pytestmark = pytest.mark.gpu
+
+RTOL64 = 1e-11
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_10741_gb300 import lattice
+    return lattice
+
+
+def _state(case, amp, seed):
+    lat = case.lattice
+    return latgen.smooth_state(lat, amp, seed).ravel()
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=float)
+    b = np.asarray(b, dtype=float)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name,amp", [("ring2", 0.01), ("ring4", 0.02), ("strut2", 0.01)])
+def test_residual_and_tangent_parity(L, name, amp):
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    u = _state(case, amp, 11)
+    lat = L.Lattice.from_case(case)
+    ud = torch.tensor(u, device="cuda")
+    out = lat.assemble_residual_tangent(ud, quad=0, residual=True, local_forces=True, tangent=True)
+    r_ref = prob.residual(u)
+    assert _rel(out["r"].cpu(), r_ref) < RTOL64
+    f_ref = OC.internal_force(prob.cell, prob.local(u), prob.mu_cells, prob.lam)
+    f_ref = f_ref.reshape(prob.lat.n_cells, -1).T
+    assert _rel(out["f"].cpu(), f_ref) < RTOL64
+    K_ref = OC.tangent(prob.cell, prob.local(u), prob.mu_cells, prob.lam)
+    assert _rel(out["K"].cpu(), K_ref) < RTOL64
+    assert abs(out["min_detF"] - OC.min_jacobian(prob.cell, prob.local(u)).min()) < 1e-12
+    # reduced rule on a subset of cells (snapshot kernel)
+    cells = np.array([prob.lat.n_cells - 1, 0], dtype=np.int32)
+    red = lat.assemble_residual_tangent(ud, quad=1, cells=torch.tensor(cells, device="cuda"), residual=False,
+                                        tangent=True)
+    Kb_ref = OC.tangent(prob.cell, prob.local(u)[cells], prob.mu_cells[cells], prob.lam, reduced=True)
+    assert _rel(red["K"].cpu(), Kb_ref) < RTOL64
+    lat.close()
+
+
+def test_gather_and_predictor_exact(L):
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    lat = L.Lattice.from_case(case)
+    u = _state(case, 0.02, 3)
+    x = lat.lattice_gather(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.array_equal(x, prob.local(u).reshape(prob.lat.n_cells, -1).T)
+    u1 = lat.lattice_predictor(case.top_displacement(1)).cpu().numpy()
+    assert np.array_equal(u1, ON.predictor(prob, 1, None, None))
+    a = torch.tensor(_state(case, 0.01, 4), device="cuda")
+    b = torch.tensor(_state(case, 0.01, 5), device="cuda")
+    u3 = lat.lattice_predictor(case.top_displacement(3), a, b).cpu().numpy()
+    assert np.abs(u3 - ON.predictor(prob, 3, a.cpu().numpy(), b.cpu().numpy())).max() < 1e-15
+    lat.close()
+
+
+def test_negative_jacobian_reported(L):
+    case = latgen.make_case("ring2")
+    lat = L.Lattice.from_case(case)
+    u = np.zeros(lat.sizes.n_dof)
+    u[0::2] = -3.0 * case.lattice.X[:, 0]          # folds every element: det F < 0
+    with pytest.raises(L.LatticeError) as e:
+        lat.assemble_residual_tangent(torch.tensor(u, device="cuda"))
+    assert e.value.code == 4
+    lat.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_greedy_parity_on_oracle_snapshots(L, seed):
+    case = latgen.make_case("ring8")
+    prob = Problem(case)
+    u = _state(case, 0.03, 20 + seed)
+    T = OC.snapshots(prob.cell, prob.local(u), prob.mu_cells, prob.lam)        # [nnz, N_s]
+    eps = 1e-3
+    g = OG.greedy(T, eps)
+    a_ref = OG.alpha_triangular(T, g)
+    lat = L.Lattice.from_case(case)
+    out = lat.greedy_select(torch.tensor(T.T.copy(), device="cuda"), eps, 64)
+    assert out["S"].cpu().numpy().tolist() == g.S.tolist()
+    assert np.abs(out["max_res"] - np.asarray(g.max_res)).max() < 1e-12
+    assert _rel(out["alpha"].cpu(), a_ref) < 1e-9
+    assert _rel(out["beta"].cpu(), g.beta) < 1e-10
+    assert _rel(out["Z"].cpu().T, g.Z) < 1e-10
+    lat.close()
+
+
+def test_greedy_degenerate_cases(L):
+    lat = L.Lattice.from_case(latgen.make_case("ring2"))
+    # identical columns up to scale: one principal, alpha = scale ratios
+    rng = np.random.default_rng(4)
+    t = rng.normal(size=40)
+    sc = rng.uniform(0.5, 2.0, 7)
+    T = np.outer(sc, t)                                   # [n_cols, n_rows]
+    out = lat.greedy_select(torch.tensor(T, device="cuda"), 1e-10, 7)
+    assert len(out["S"]) == 1
+    s0 = int(out["S"][0])
+    assert np.abs(out["alpha"].cpu().numpy()[0] - sc / sc[s0]).max() < 1e-12
+    # orthogonal columns, ties broken to the lowest index, cap respected
+    out = lat.greedy_select(torch.eye(5, dtype=torch.float64, device="cuda"), 0.1, 3)
+    assert out["S"].cpu().tolist() == [0, 1, 2]
+    lat.close()
+
+
+def _select_and_reference(L, name, amp, seed, eps, precision=0):
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    u = _state(case, amp, seed)
+    lat = L.Lattice.from_case(case, precision)
+    sel = lat.select_principal_cells(torch.tensor(u, device="cuda"), eps, 128)
+    T = OC.snapshots(prob.cell, prob.local(u), prob.mu_cells, prob.lam)
+    g = OG.greedy(T, eps, 128)
+    a_ref = OG.alpha_triangular(T, g)
+    Kp_ref = OC.tangent(prob.cell, prob.local(u)[g.S], prob.mu_cells[g.S], prob.lam)
+    return case, prob, lat, sel, g, a_ref, Kp_ref
+
+
+def test_select_principal_cells_parity(L):
+    case, prob, lat, sel, g, a_ref, Kp_ref = _select_and_reference(L, "ring8", 0.03, 7, 1e-3)
+    assert sel["S"].cpu().numpy().tolist() == g.S.tolist()
+    assert _rel(sel["alpha"].cpu(), a_ref) < 1e-9
+    assert _rel(sel["Kp"].cpu(), Kp_ref) < RTOL64
+    lat.close()
+
+
+@pytest.mark.parametrize("name", ["ring8", "strut2"])
+def test_reduced_apply_parity(L, name):
+    case, prob, lat, sel, g, a_ref, Kp_ref = _select_and_reference(L, name, 0.02, 8, 1e-3)
+    assert sel["S"].cpu().numpy().tolist() == g.S.tolist()
+    s = lat.sizes
+    X = latgen.uniform_field((s.n_loc, s.n_cells), 7)
+    Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda")).cpu().numpy()
+    Y_ref = OR.reduced_apply(prob.cell, Kp_ref, a_ref, X)
+    assert _rel(Y, Y_ref) < 1e-10
+    lat.close()
+    # FP32 action from a mixed-precision handle
+    case, prob, lat, sel, g, a_ref, Kp_ref = _select_and_reference(L, name, 0.02, 8, 1e-3, precision=1)
+    Y32 = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=torch.float32)).cpu().numpy()
+    assert _rel(Y32, Y_ref) < 2e-6
+    lat.close()
+
+
+def test_force_all_apply_is_per_cell(L):
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    u = _state(case, 0.02, 9)
+    lat = L.Lattice.from_case(case)
+    sel = lat.select_principal_cells(torch.tensor(u, device="cuda"), 0.0, 1, force_all=True)
+    assert sel["n_r"] == prob.lat.n_cells
+    K = OC.tangent(prob.cell, prob.local(u), prob.mu_cells, prob.lam)
+    X = latgen.uniform_field((lat.sizes.n_loc, lat.sizes.n_cells), 7)
+    Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda")).cpu().numpy()
+    Y_ref = np.stack([prob.cell.dense(K[s]) @ X[:, s] for s in range(prob.lat.n_cells)], axis=1)
+    assert _rel(Y, Y_ref) < RTOL64
+    lat.close()
+
+
+def test_full_size_ring32_sampled(L):
+    """The 32x32 ring lattice (0.56 M DOF) at full size: residual, tangents and snapshots of 64
+    seeded cells, the greedy on the full snapshot matrix and the apply on sampled cells."""
+    case = latgen.make_case("ring32")
+    prob = Problem(case)
+    u = ON.predictor(prob, 2, None, None) + 0.002 * latgen.uniform_field(prob.n_dof, 13)
+    u[prob.fixed] = ON.predictor(prob, 2, None, None)[prob.fixed]
+    lat = L.Lattice.from_case(case)
+    ud = torch.tensor(u, device="cuda")
+    cells = np.sort(np.random.default_rng(14).choice(prob.lat.n_cells, 64, replace=False)).astype(np.int32)
+    out = lat.assemble_residual_tangent(ud, local_forces=True, tangent=False)
+    ul = prob.local(u)
+    f_ref = OC.internal_force(prob.cell, ul[cells], prob.mu_cells[cells], prob.lam).reshape(64, -1).T
+    assert _rel(out["f"].cpu().numpy()[:, cells], f_ref) < RTOL64
+    ct = torch.tensor(cells, device="cuda")
+    Kf = lat.assemble_residual_tangent(ud, quad=0, cells=ct, residual=False, tangent=True)["K"].cpu()
+    assert _rel(Kf, OC.tangent(prob.cell, ul[cells], prob.mu_cells[cells], prob.lam)) < RTOL64
+    sel = lat.select_principal_cells(ud, 3e-4, 256)
+    assert 1 <= sel["n_r"] <= 256
+    # the principal set is a valid greedy trace: every selected cell is principal with alpha = e_r
+    al = sel["alpha"].cpu().numpy()
+    S = sel["S"].cpu().numpy()
+    assert np.abs(al[:, S] - np.eye(len(S))).max() < 1e-9
+    Kp = sel["Kp"].cpu().numpy()
+    assert _rel(Kp[:4], OC.tangent(prob.cell, ul[S[:4]], prob.mu_cells[S[:4]], prob.lam)) < RTOL64
+    X = latgen.uniform_field((lat.sizes.n_loc, lat.sizes.n_cells), 7)
+    Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda")).cpu().numpy()
+    Y_ref = OR.reduced_apply(prob.cell, Kp, al[:, cells], X[:, cells])
+    assert _rel(Y[:, cells], Y_ref) < 1e-10
+    lat.close()

@@ -1,0 +1,190 @@
+"""GPU parity of the FETI-DP pieces, the Krylov solve, Newton load stepping and the adjoint.
+
+The reference is the FP64 CPU oracle: direct sparse solves of the assembled system (exact
+tangent, or the reduced tangents sum_r alpha_r^s K^r of the oracle's own greedy), Newton with
+Armijo backtracking, and the direct adjoint.  Tolerances follow from the solver tolerances:
+the Krylov relative residual 1e-12 gives directions within ~1e-9; Newton solutions converged to
+1e-12 agree to 1e-10 relative L2 (FP64 mode); in the mixed modes only the preconditioner is
+FP32 (the Krylov operator, residual and update stay FP64), so the solution converges to the
+Newton tolerance (1e-8 relative residual) of the oracle's solution.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+import latgen
+from oracle import adjoint as OA
+from oracle import cell as OC
+from oracle import greedy as OG
+from oracle import newton as ON
+from oracle import rom as OR
+from oracle.assembly import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2603_10741_gb300 import lattice
+    return lattice
+
+
+def _u0(prob, step=1, jitter=0.0, seed=0):
+    u = ON.predictor(prob, step, None, None)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        u[prob.free] += jitter * rng.uniform(-1, 1, prob.free.size)
+    return u
+
+
+def test_jump_of_continuous_vector_is_zero_and_roundtrip(L):
+    case = latgen.make_case("strut2")
+    prob = Problem(case)
+    lat = L.Lattice.from_case(case)
+    u = latgen.smooth_state(case.lattice, 0.01, 1).ravel()
+    u[prob.fixed] = 0
+    ud = torch.tensor(u, device="cuda")
+    lat.select_principal_cells(ud, 1e-3)
+    lat.lattice_prepare_solver(ud)
+    v = lat.feti_from_global(ud)
+    s = lat.sizes
+    w = lat.feti_apply(0, v).cpu().numpy()
+    lam = w[s.n_loc * s.n_cells + s.n_primal:]
+    assert lam.size == s.n_lambda and np.abs(lam).max() < 1e-15
+    back = lat.feti_to_global(v).cpu().numpy()
+    assert np.abs(back - u).max() < 1e-15
+    lat.close()
+
+
+@pytest.mark.parametrize("name", ["ring4", "strut2"])
+def test_force_all_local_inverse_is_exact(L, name):
+    """With every cell principal, K^-rom is the exact partially assembled inverse (Section 3.3.1)."""
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    lat = L.Lattice.from_case(case)
+    ud = torch.tensor(_u0(prob, 1, 0.002, 1), device="cuda")
+    lat.select_principal_cells(ud, 0.0, 1, force_all=True)
+    lat.lattice_prepare_solver(ud)
+    s = lat.sizes
+    rng = np.random.default_rng(3)
+    v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
+    # remove the multiplier part, apply K~ then K^-rom
+    v[s.n_loc * s.n_cells + s.n_primal:] = 0
+    Kv = lat.feti_apply(0, v)
+    Kv[s.n_loc * s.n_cells + s.n_primal:] = 0
+    back = lat.feti_apply(1, Kv)
+    nd = s.n_loc * s.n_cells + s.n_primal
+    err = (back[:nd] - v[:nd]).abs().max().item() / v[:nd].abs().max().item()
+    assert err < 1e-9
+    lat.close()
+
+
+@pytest.mark.parametrize("force_all", [True, False])
+@pytest.mark.parametrize("name", ["ring4", "strut2"])
+def test_krylov_solve_matches_direct_solve(L, name, force_all):
+    """The FGMRES solution on the FETI-DP saddle point equals the oracle's direct solve of the
+    assembled (exact, or reduced sum_r alpha_r^s K^r) tangent system for the Newton rhs -r."""
+    case = latgen.make_case(name)
+    # a state below the first local instability: with corner-only primal DOFs the thin strut
+    # cells' remaining-DOF matrices lose definiteness near 1 % compression (Section 3.3.2)
+    case.total_strain = 0.01 if name == "ring4" else 0.002
+    prob = Problem(case)
+    u0 = _u0(prob, 1, 0.0005 if name == "ring4" else 0.0001, 2)
+    lat = L.Lattice.from_case(case)
+    eps = 1e-3
+    opts = lat.lattice_default_opts(eps=eps, force_all=int(force_all), krylov_rtol=1e-12, krylov_max_it=3000)
+    ud = torch.tensor(u0, device="cuda")
+    sel = lat.select_principal_cells(ud, eps, 256, force_all=force_all)
+    lat.lattice_prepare_solver(ud, opts)
+    r = prob.residual(u0)
+    x, its, rel = lat.tangent_solve(torch.tensor(-r, device="cuda"), opts)
+    assert rel <= 1e-12
+    x = x.cpu().numpy()
+    free = prob.free
+    if force_all:
+        A = prob.tangent(u0)
+    else:
+        ul = prob.local(u0)
+        T = OC.snapshots(prob.cell, ul, prob.mu_cells, prob.lam)
+        g = OG.greedy(T, eps, 256)
+        assert sel["S"].cpu().numpy().tolist() == g.S.tolist()
+        al = OG.alpha_triangular(T, g)
+        Kp = OC.tangent(prob.cell, ul[g.S], prob.mu_cells[g.S], prob.lam)
+        A = OR.assembled(prob, OR.reduced_tangents(Kp, al))
+    ref = spla.spsolve(A[free][:, free].tocsc(), -r[free])
+    assert np.abs(x[free] - ref).max() < 1e-9 * np.abs(ref).max()
+    assert np.all(x[prob.fixed] == 0)
+    lat.close()
+
+
+@pytest.mark.parametrize("force_all", [True, False])
+def test_newton_load_path_ring4_fp64(L, force_all):
+    """The 4x4 ring lattice, 8x8 Q1 per cell, -10 % in 10 steps: the GPU load path (plain full
+    tangent or reduced basis, FP64) reaches the oracle's solution at every step."""
+    from paper_2603_10741_gb300 import solve_load_path
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, ref_reps = ON.load_path(prob, tol=1e-12)
+    lat = L.Lattice.from_case(case)
+    opts = lat.lattice_default_opts(newton_rtol=1e-12, force_all=int(force_all), krylov_rtol=1e-12)
+    states = []
+    u, reps = solve_load_path(lat, case, opts, log=lambda k, rep: None)
+    got = u.cpu().numpy()
+    err = np.linalg.norm(got - ref[-1]) / np.linalg.norm(ref[-1])
+    assert err < 1e-10, err
+    its = sum(r["iterations"] for r in reps)
+    its_ref = sum(r.iterations for r in ref_reps)
+    if force_all:
+        assert its <= its_ref + 2              # exact Newton, same iteration counts
+    else:
+        assert its <= 4 * its_ref              # quasi-Newton with the reduced tangent
+    lat.close()
+
+
+@pytest.mark.parametrize("precision", [1])
+def test_newton_mixed_precision_ring4(L, precision):
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, _ = ON.load_path(prob, n_steps=3, tol=1e-12)
+    from paper_2603_10741_gb300 import solve_load_path
+    lat = L.Lattice.from_case(case, precision)
+    opts = lat.lattice_default_opts(newton_rtol=1e-10)
+    u, reps = solve_load_path(lat, case, opts, steps=3)
+    got = u.cpu().numpy()
+    err = np.linalg.norm(got - ref[-1]) / np.linalg.norm(ref[-1])
+    assert err < 1e-8, err
+    r = prob.residual(got)
+    r0 = prob.residual(ON.predictor(prob, 3, ref[1], ref[0]))
+    assert np.linalg.norm(r[prob.free]) <= 1e-8 * np.linalg.norm(r0[prob.free])
+    lat.close()
+
+
+def test_adjoint_gradient_matches_oracle(L):
+    case = latgen.make_case("ring2")
+    prob = Problem(case)
+    states, _ = ON.load_path(prob, tol=1e-13)
+    u = states[-1]
+    g_ref = OA.gradient(prob, u)
+    J_ref = ON.compliance(prob, u)
+    lat = L.Lattice.from_case(case)
+    opts = lat.lattice_default_opts(eps=1e-4)
+    g, J, rep = lat.adjoint_gradient(torch.tensor(u, device="cuda"), opts)
+    assert rep.converged
+    assert abs(J - J_ref) < 1e-12 * abs(J_ref)
+    assert np.abs(g.cpu().numpy() - g_ref).max() < 1e-9 * np.abs(g_ref).max()
+    lat.close()
+
+
+def test_checkpoint_roundtrip(L, tmp_path):
+    case = latgen.make_case("ring2")
+    lat = L.Lattice.from_case(case)
+    a = torch.rand(lat.sizes.n_dof, dtype=torch.float64, device="cuda")
+    b = torch.rand(lat.sizes.n_dof, dtype=torch.float64, device="cuda")
+    lat.lattice_checkpoint_save(tmp_path / "c.ckpt", 3, -0.25, a, b)
+    step, load, a2, b2 = lat.lattice_checkpoint_load(tmp_path / "c.ckpt")
+    assert step == 3 and load == -0.25
+    assert torch.equal(a, a2) and torch.equal(b, b2)
+    lat.close()
