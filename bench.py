@@ -1,0 +1,467 @@
+"""Benchmark: one Newton iteration of the reduced-order FETI-DP hot path on one GB300.
+
+Workload: the 2D lattice of 32 x 32 ring cells (unit squares with a central hole r = 0.3), 16 x 16
+mapped Q1 quads per cell, 556 034 DOF, per-cell shear modulus factors theta_s ~ U[0.9, 1.1]
+(seed 2), plane-strain neo-Hookean mu = 1, lam = 4, bottom clamped, top displaced -20 % in 20
+steps.  The load path is run on the GPU up to load step ``--state-step`` (untimed); a step of
+the benchmark is then one full Newton iteration from the predictor of the next load step:
+residual, snapshots + greedy + coefficients, principal tangents, FETI-DP preconditioner setup,
+FGMRES with the reduced tangent, Armijo line search and update.  Every step starts from the same
+state, so every step does the same work.
+
+Reported: the reduced path in FP64 (the headline), the plain FP64 full-tangent path (every cell
+principal, exact local solves) and the mixed FP32 reduced path on the same state; the reduced
+tangent action alone (GDOF/s, FP64 and FP32, L2 flushed between calls); per-kernel times from
+CUDA events on the library's stream; an end-to-end number through host buffers; the FP64 CPU
+oracle on a bounded sample; clocks sampled during the timed region.
+
+``--impl reference`` times the oracle (plain FP64 numpy/scipy Newton iteration with sparse LU)
+on the host cores instead: each step is one oracle Newton iteration on the same lattice.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reduced tangent-apply GDOF/s & Newton-step time vs plain FP64 GPU path, 1 GB300"
+WORKLOAD = ("ring32: 2D 32x32 ring cells (hole r=0.3), 16x16 Q1 per cell, 556034 DOF, "
+            "theta~U[0.9,1.1] seed 2, mu=1 lam=4, -20% in 20 steps")
+
+# peaks: measured copy bandwidth / bf16 GEMM (driver file), FP64/FP32 ALU from unit counts
+FP64_PEAK_TFLOPS = 1.25      # GB300 FP64 (recipe table); 1.20 measured with an FMA loop
+FP32_PEAK_TFLOPS = 80.5      # 152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--case", default="ring32")
+    p.add_argument("--state-step", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--quick", action="store_true", help="skip the full-path and mixed comparisons")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, dev_index=0):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(dev_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows)
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def dist_init(args):
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif args.impl == "ours":
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x, dev=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle
+# ---------------------------------------------------------------------------------------------
+def oracle_step_fn(case_name, state_step):
+    """One oracle Newton iteration (residual, assembled tangent, sparse LU, Armijo) from the
+    affine predictor of load step state_step+1; returns (fn, n_dof)."""
+    import numpy as np
+    import scipy.sparse.linalg as spla
+
+    import latgen
+    from oracle import newton as ON
+    from oracle.assembly import Problem
+    case = latgen.make_case(case_name)
+    prob = Problem(case)
+    u0 = ON.predictor(prob, state_step + 1, None, None)
+
+    def step():
+        r = prob.residual(u0)
+        K = prob.tangent(u0)
+        free = prob.free
+        du = spla.splu(K[free][:, free].tocsc()).solve(-r[free])
+        rn = np.linalg.norm(r[free])
+        for m in range(31):
+            t = 0.5 ** m
+            ut = u0.copy()
+            ut[free] += t * du
+            if prob.min_jacobian(ut) > 0 and np.linalg.norm(prob.residual(ut)[free]) <= (1 - 1e-4 * t) * rn:
+                break
+        return ut
+
+    return step, prob.n_dof
+
+
+def threads_in_use():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info()]
+        return max(n) if n else 1
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init(args)
+    if rank != 0:
+        barrier(ws)
+        return 0
+    step, n_dof = oracle_step_fn(args.case, args.state_step)
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = n_dof * args.steps / dt / 1e9
+    cores = threads_in_use()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": "one oracle Newton iteration (residual, assembled tangent, "
+                   "sparse LU solve, Armijo) from the affine predictor of load step %d" % (args.state_step + 1)},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": cores, "kind": "oracle",
+                         "sample": "%d oracle Newton iterations on the full lattice" % args.steps},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    barrier(ws)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
+           "local_segmm", "local_gemv", "gj_update", "krylov_orth"]
+
+
+def kernel_work(name, s, n_r, n_keys, prec_bytes):
+    """Algorithmic work per launch (bytes or flops) and its roofline (bound, peak unit).
+
+    local_segmm / local_gemv: the principal-block x cell-multivector product, 2 (n_R + n_P) n_R
+        flops per cell (dense local inverse and coarse restriction);
+    apply_reduced: 2 N_r nnz flops per cell (Eq. romstiffnessmatrix), bytes = X + Y + alpha;
+    apply_percell: the plain path, 2 nnz flops and 8 nnz bytes of K^s per cell;
+    residual: bytes of u gathered and f written (FP64 ALU bound: see the design doc).
+    """
+    n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
+    rows = s.n_r_local + s.n_p_local
+    if name in ("local_segmm", "local_gemv"):
+        return 2.0 * rows * s.n_r_local * n_s, "flops"
+    if name == "apply_reduced":
+        return 2.0 * n_r * nnz * n_s, "flops"
+    if name == "apply_percell":
+        return 8.0 * nnz * n_s + 2 * 8.0 * n_loc * n_s, "bytes"
+    return None, None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    import latgen
+    from paper_2603_10741_gb300 import LAT_FP64, LAT_MIXED_FP32, Lattice, solve_load_path
+
+    ws, rank, local = dist_init(args)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hbm_peak, bf16_peak, peak_src = peaks()
+    case = latgen.make_case(args.case)
+    stream = torch.cuda.current_stream()
+
+    # state: converged load steps 1..state_step (mixed precision path, untimed)
+    lat_m = Lattice.from_case(case, LAT_MIXED_FP32)
+    opts_m = lat_m.lattice_default_opts()
+    u_prev, u_prev2 = None, None
+    for k in range(1, args.state_step + 1):
+        u = lat_m.lattice_predictor(case.top_displacement(k), u_prev, u_prev2)
+        rep = lat_m.newton_step(u, opts_m)
+        if not rep.converged:
+            raise RuntimeError(f"load path failed at step {k}")
+        u_prev2, u_prev = u_prev, u
+    u_start = lat_m.lattice_predictor(case.top_displacement(args.state_step + 1), u_prev, u_prev2).clone()
+    torch.cuda.synchronize()
+
+    def time_newton(lat, opts, steps, warmup, clocks=None, timing=False):
+        u = torch.empty_like(u_start)
+        reps = []
+        for _ in range(warmup):
+            u.copy_(u_start)
+            lat.newton_step(u, opts, max_iterations=1)
+        torch.cuda.synchronize()
+        barrier(ws)
+        if timing:
+            lat.lattice_set_timing(True)
+        if clocks:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            u.copy_(u_start)
+            reps.append(lat.newton_step(u, opts, max_iterations=1).as_dict())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ck = clocks.stop(local) if clocks else None
+        barrier(ws)
+        ms = e0.elapsed_time(e1)
+        ktimes = {}
+        if timing:
+            for kname in KERNELS:
+                t, n = lat.lattice_kernel_time(kname)
+                if n:
+                    ktimes[kname] = {"total_ms": t / steps, "launches": n / steps, "avg_us": 1e3 * t / n}
+            lat.lattice_set_timing(False)
+        return max_over_ranks(ws, ms, dev) / steps, reps, ktimes, ck
+
+    n_dof = lat_m.sizes.n_dof
+    s = lat_m.sizes
+    # headline: reduced path, FP64
+    lat = Lattice.from_case(case, LAT_FP64)
+    opts = lat.lattice_default_opts()
+    clocks = Clocks()
+    ms_red, reps_red, kt_red, ck = time_newton(lat, opts, args.steps, args.warmup, clocks, timing=True)
+    value = ws * n_dof / (ms_red * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_red, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 reduced (EIM) path", "eps": opts.eps,
+                   "step": "one Newton iteration (residual, snapshots+greedy+alpha, principal tangents, "
+                           "FETI-DP setup, FGMRES, Armijo, update) from the predictor of load step %d"
+                           % (args.state_step + 1),
+                   "l2": "working set > L2 (FGMRES basis %.0f MB, local inverses)"
+                         % (2 * (opts.krylov_restart + 1) * s.n_krylov * 8 / 1e6),
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "newton": {"n_r": reps_red[-1]["n_r_last"], "krylov_its": reps_red[-1]["krylov_its_total"],
+                   "armijo_m": reps_red[-1]["armijo_m_max"],
+                   "phase_ms": {k: reps_red[-1][k] for k in ("t_residual_ms", "t_select_ms", "t_setup_ms",
+                                                            "t_krylov_ms", "t_linesearch_ms")},
+                   "kernels": kt_red},
+    }
+    # dominant kernel roofline (FP64 ALU for the principal-block products)
+    dom = max(kt_red.items(), key=lambda kv: kv[1]["total_ms"])[0] if kt_red else None
+    if dom:
+        work, kind = kernel_work(dom, s, out["newton"]["n_r"], None, 8)
+        if work is not None:
+            avg_s = kt_red[dom]["avg_us"] * 1e-6
+            if kind == "flops":
+                ach = work / avg_s / 1e12
+                out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                                   "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                                   "peak_source": "FP64 ALU, recipe table (1.20 measured)",
+                                   "work_per_launch": work}
+            else:
+                ach = work / avg_s / 1e9
+                out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                                   "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                                   "peak_source": peak_src, "work_per_launch": work}
+    out["clocks"] = ck
+    # launches per step, counted with the CUDA profiler on one extra step
+    out["gpu_launches"] = count_launches(lat, opts, u_start) * args.steps
+
+    if not args.quick:
+        # plain FP64 full-tangent path on the same state
+        ms_full, reps_full, kt_full, _ = time_newton(lat, lat.lattice_default_opts(force_all=1),
+                                                     max(2, args.steps // 2), 1, None, timing=True)
+        out["fp64_full_path"] = {"ms_per_step": ms_full, "value": ws * n_dof / (ms_full * 1e-3) / 1e9,
+                                 "krylov_its": reps_full[-1]["krylov_its_total"],
+                                 "phase_ms": {k: reps_full[-1][k] for k in ("t_residual_ms", "t_select_ms",
+                                                                            "t_setup_ms", "t_krylov_ms")},
+                                 "kernels": kt_full}
+        out["speedup_vs_fp64_full"] = ms_full / ms_red
+        # mixed precision reduced path
+        ms_mix, reps_mix, kt_mix, _ = time_newton(lat_m, opts_m, args.steps, 1, None, timing=True)
+        out["mixed_fp32"] = {"ms_per_step": ms_mix, "value": ws * n_dof / (ms_mix * 1e-3) / 1e9,
+                             "krylov_its": reps_mix[-1]["krylov_its_total"], "n_r": reps_mix[-1]["n_r_last"],
+                             "phase_ms": {k: reps_mix[-1][k] for k in ("t_residual_ms", "t_select_ms",
+                                                                       "t_setup_ms", "t_krylov_ms")},
+                             "kernels": kt_mix}
+    # reduced tangent action alone (selection of the benchmark state), L2 flushed between calls
+    out["apply"] = bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src)
+    # end to end through host buffers: H2D of the state, one Newton iteration, D2H of the result
+    out["e2e"] = bench_e2e(lat, opts, u_start, args, ws, dev, n_dof)
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(out))
+    lat.close()
+    lat_m.close()
+    return 0
+
+
+def count_launches(lat, opts, u_start):
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        u = u_start.clone()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            lat.newton_step(u, opts, max_iterations=1)
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            if e.device_type.name == "CUDA" and not e.name.startswith(("Memcpy", "Memset", "memcpy", "memset")):
+                n += 1
+        return n
+    except Exception:
+        return None
+
+
+def bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src):
+    """apply_reduced_tangent on the benchmark state's selection, FP64 and FP32."""
+    import torch
+    res = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for tag, L, dt, eb in (("fp64", lat, torch.float64, 8), ("fp32", lat_m, torch.float32, 4)):
+        sel = L.select_principal_cells(u_start, L.lattice_default_opts().eps, 256)
+        n_r = sel["n_r"]
+        x = torch.rand((s.n_loc, s.n_cells), dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(5):
+            L.apply_reduced_tangent(x, y)
+        times = []
+        for _ in range(50):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            L.apply_reduced_tangent(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        t = statistics.median(times)
+        stacked = s.n_loc * s.n_cells
+        flops = 2.0 * n_r * s.nnz * s.n_cells
+        byts = 2.0 * eb * stacked + eb * n_r * s.n_cells + eb * n_r * s.nnz
+        alu_peak = FP64_PEAK_TFLOPS if tag == "fp64" else FP32_PEAK_TFLOPS
+        res[tag] = {"gdofs": stacked / t / 1e9, "us": t * 1e6, "n_r": n_r,
+                    "roofline": {"hbm": {"achieved_gbs": byts / t / 1e9, "peak": hbm_peak, "frac": byts / t / 1e9 / hbm_peak,
+                                         "bytes": byts, "peak_source": peak_src},
+                                 "alu": {"achieved_tflops": flops / t / 1e12, "peak": alu_peak,
+                                         "frac": flops / t / 1e12 / alu_peak, "flops": flops},
+                                 "binding": max(byts / (hbm_peak * 1e9), flops / (alu_peak * 1e12)) / t}}
+    del flush
+    return res
+
+
+def bench_e2e(lat, opts, u_start, args, ws, dev, n_dof):
+    import torch
+    host = u_start.cpu().pin_memory()
+    out_host = torch.empty_like(host).pin_memory()
+    u = torch.empty_like(u_start)
+    stream = torch.cuda.current_stream()
+    for _ in range(1):
+        u.copy_(host, non_blocking=True)
+        lat.newton_step(u, opts, max_iterations=1)
+        out_host.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        u.copy_(host, non_blocking=True)
+        lat.newton_step(u, opts, max_iterations=1)
+        out_host.copy_(u, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(ws, e0.elapsed_time(e1), dev) / args.steps
+    nb = n_dof * 8
+    return {"value": ws * n_dof / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms,
+            "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+
+def cpu_baseline(args):
+    step, n_dof = oracle_step_fn(args.case, args.state_step)
+    t0 = time.perf_counter()
+    step()
+    dt = time.perf_counter() - t0
+    return {"value": n_dof / dt / 1e9, "unit": "GDOF/s", "cores": threads_in_use(), "kind": "oracle",
+            "sample": "one oracle Newton iteration (residual, assembled tangent, sparse LU, Armijo) on the "
+                      "full lattice from the affine predictor of load step %d, %.1f s" % (args.state_step + 1, dt)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -211,6 +211,14 @@ lat_status feti_to_global(lat_handle h, const double* v, double* u_glob);
 /* Map a global vector to the saddle-point layout (copies on every cell, multipliers 0). */
 lat_status feti_from_global(lat_handle h, const double* u_glob, double* v);
 
+/* Kernel timing: while enabled, CUDA events are recorded on the handle's stream around every
+ * launch of the named kernels ("residual", "tangent_full", "tangent_reduced", "greedy_update",
+ * "apply_reduced", "apply_percell", "local_segmm", "local_gemv", "gj_update", "krylov_orth").
+ * lattice_set_timing clears the records; lattice_kernel_time returns the summed duration (host
+ * ms) and the launch count of one name since then. */
+lat_status lattice_set_timing(lat_handle h, int32_t enable);
+lat_status lattice_kernel_time(lat_handle h, const char* name, double* total_ms, int32_t* launches);
+
 /* Load-step checkpoint: the step index, the load parameter and the last two converged states
  * (dev [n_dof]; u_prev may be NULL) to/from a binary file. */
 lat_status lattice_checkpoint_save(lat_handle h, const char* path, int32_t step, double load,

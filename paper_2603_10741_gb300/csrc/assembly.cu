@@ -420,6 +420,7 @@ void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_g
   h->minJ_cell.ensure(h->n_cells);
   auto g = geom(h, 0);
   auto ct = colors(h);
+  KernelTimer kt(h, "residual");
   if (h->dim == 2) {
     k_residual<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
         h->cell_nodes.p, h->mu_cell.p, -1.0, h->lam, u_glob, f_cells, h->minJ_cell.p);
@@ -451,6 +452,7 @@ void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, i
   h->minJ_cell.ensure(std::max(h->n_cells, n_sel));
   auto g = geom(h, quad);
   auto ct = colors(h);
+  KernelTimer kt(h, quad ? "tangent_reduced" : "tangent_full");
   if (h->dim == 2) {
     k_tangent<2><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
         cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p);

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -149,6 +150,40 @@ struct lat_ctx {
   bool indefinite = false;
   bool verbose = false;               // LATTICE_VERBOSE=1: per-iteration log on stderr           // some local or coarse pivot was negative
   double *h_pinned = nullptr;          // small pinned host scratch
+
+  // optional per-kernel timing: CUDA events recorded on the launching stream around the
+  // launches of named kernels (lattice_set_timing / lattice_kernel_time)
+  bool timing = false;
+  std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// RAII bracket: records a start event now and a stop event at scope exit when timing is on
+struct KernelTimer {
+  lat_ctx* h;
+  const char* name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  static cudaEvent_t take(lat_ctx* h) {
+    if (!h->ev_pool.empty()) {
+      cudaEvent_t e = h->ev_pool.back();
+      h->ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  KernelTimer(lat_ctx* h_, const char* n) : h(h_), name(n) {
+    if (!h->timing) return;
+    a = take(h);
+    b = take(h);
+    cudaEventRecord(a, h->stream);
+  }
+  ~KernelTimer() {
+    if (!a) return;
+    cudaEventRecord(b, h->stream);
+    h->ev[name].push_back({a, b});
+  }
 };
 
 // run f, converting LatError and std exceptions into a status and h->err

@@ -298,7 +298,7 @@ __global__ void k_densify(int n_keys, const int* __restrict__ key_list, int n_cl
   const int r = key / n_classes, cl = key % n_classes;
   const int rep = class_rep[cl];
   const double* K = Kp + (size_t)r * nnz;
-  double* g = G + (size_t)k * n_R * n_R;
+  double* g = G + (size_t)k * (n_R + n_P) * n_R;
   double* krp = KRP + (size_t)k * n_R * n_P;
   double* kpp = KPP + (size_t)k * n_P * n_P;
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
@@ -333,11 +333,11 @@ __global__ void k_densify(int n_keys, const int* __restrict__ key_list, int n_cl
 // A_pj = Pi A_pj;  A_ip = -A_ip Pi;  A_pp = Pi.
 constexpr int GJB = 32;
 
-__global__ void k_gj_pivot(int n, int k0, int kw, double* __restrict__ A, double* __restrict__ Pinv,
+__global__ void k_gj_pivot(int n, int64_t bs, int k0, int kw, double* __restrict__ A, double* __restrict__ Pinv,
                            double* __restrict__ Cbuf, int* __restrict__ flag) {
   __shared__ double M[GJB][GJB + 1];
   const int b = blockIdx.x;
-  double* a = A + (size_t)b * n * n;
+  double* a = A + (size_t)b * bs;
   const int t = threadIdx.x;  // 1024 threads: (i, j)
   const int i = t / GJB, j = t % GJB;
   if (i < kw && j < kw) M[i][j] = a[(size_t)(k0 + i) * n + k0 + j];
@@ -373,10 +373,10 @@ __global__ void k_gj_pivot(int n, int k0, int kw, double* __restrict__ A, double
 }
 
 // Rbuf[b][m][j] = sum_l Pinv[m][l] A[k0+l][j]  (new pivot rows)
-__global__ void k_gj_rows(int n, int k0, int kw, const double* __restrict__ A, const double* __restrict__ Pinv,
-                          double* __restrict__ Rbuf) {
+__global__ void k_gj_rows(int n, int64_t bs, int k0, int kw, const double* __restrict__ A,
+                          const double* __restrict__ Pinv, double* __restrict__ Rbuf) {
   const int b = blockIdx.y;
-  const double* a = A + (size_t)b * n * n;
+  const double* a = A + (size_t)b * bs;
   const double* P = Pinv + (size_t)b * GJB * GJB;
   __shared__ double Ps[GJB][GJB];
   for (int t = threadIdx.x; t < GJB * GJB; t += blockDim.x) Ps[t / GJB][t % GJB] = (t / GJB < kw && t % GJB < kw) ? P[t] : 0.0;
@@ -400,11 +400,11 @@ __global__ void k_gj_rows(int n, int k0, int kw, const double* __restrict__ A, c
 }
 
 // trailing update over 64x64 tiles; every tile reads only Cbuf / Rbuf / Pinv, so tiles are independent
-__global__ void __launch_bounds__(256) k_gj_update(int n, int k0, int kw, double* __restrict__ A,
+__global__ void __launch_bounds__(256) k_gj_update(int n, int64_t bs, int k0, int kw, double* __restrict__ A,
                                                    const double* __restrict__ Pinv, const double* __restrict__ Cbuf,
                                                    const double* __restrict__ Rbuf) {
   const int b = blockIdx.z;
-  double* a = A + (size_t)b * n * n;
+  double* a = A + (size_t)b * bs;
   const double* C = Cbuf + (size_t)b * n * GJB;
   const double* R = Rbuf + (size_t)b * GJB * n;
   const double* P = Pinv + (size_t)b * GJB * GJB;
@@ -459,18 +459,21 @@ __global__ void __launch_bounds__(256) k_gj_update(int n, int k0, int kw, double
   }
 }
 
-// Phi = -G K_RP   [k][n_R][n_P]
-__global__ void k_phi(int n_R, int n_P, const double* __restrict__ G, const double* __restrict__ KRP,
+// Phi = -G K_RP [k][n_R][n_P]; Phi^T is also stored as rows n_R.. of the augmented local
+// matrix [G; Phi^T] ((n_R + n_P) x n_R per key), so that one GEMM gives G x and Phi^T x
+__global__ void k_phi(int n_R, int n_P, double* __restrict__ G, const double* __restrict__ KRP,
                       double* __restrict__ Phi) {
   const int k = blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_R * n_P) return;
   const int i = t / n_P, j = t % n_P;
-  const double* g = G + (size_t)k * n_R * n_R + (size_t)i * n_R;
+  double* gk = G + (size_t)k * (n_R + n_P) * n_R;
+  const double* g = gk + (size_t)i * n_R;
   const double* b = KRP + (size_t)k * n_R * n_P;
   double v = 0;
   for (int l = 0; l < n_R; ++l) v += g[l] * b[(size_t)l * n_P + j];
   Phi[(size_t)k * n_R * n_P + t] = -v;
+  gk[(size_t)(n_R + j) * n_R + i] = -v;
 }
 
 // S = K_PP + K_RP^T Phi  (in place on KPP)   [k][n_P][n_P]
@@ -512,70 +515,81 @@ __global__ void k_d2f(int64_t n, const double* __restrict__ x, float* __restrict
 // ---------------------------------------------------------------------------------------------
 // K^-rom application kernels
 // ---------------------------------------------------------------------------------------------
-// plain path / many keys: one CTA per cell, y_R = (1/c_s) G^{slot(s)} x_R  (warp per row)
+// Local part of K^-rom and the coarse restriction in one product with the augmented matrix
+// [G; Phi^T] of the cell's key:  rows i < n_R give y_R = (1/c_s) G x_R (written to the cell's
+// remaining rows), rows n_R + j give (Phi^T x_R)_j (written to the cell's corner rows, unscaled).
+__device__ __forceinline__ size_t out_row(int i, int n_R, const int* __restrict__ rdofs,
+                                          const int* __restrict__ pdofs) {
+  return (size_t)(i < n_R ? rdofs[i] : pdofs[i - n_R]);
+}
+
+// plain path / many keys: one CTA per cell, warp per row
 template <typename TG>
 __global__ void __launch_bounds__(256)
-    k_local_gemv(int n_cells, int n_R, const TG* __restrict__ G, const int* __restrict__ slot,
-                 const double* __restrict__ cscale, const int* __restrict__ rdofs,
+    k_local_gemv(int n_cells, int n_R, int n_P, const TG* __restrict__ G, const int* __restrict__ slot,
+                 const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
                  const double* __restrict__ X, double* __restrict__ Y) {
   extern __shared__ double xs[];
   const int s = blockIdx.x;
   for (int k = threadIdx.x; k < n_R; k += blockDim.x) xs[k] = X[(size_t)rdofs[k] * n_cells + s];
   __syncthreads();
-  const TG* g = G + (size_t)slot[s] * n_R * n_R;
+  const int rows = n_R + n_P;
+  const TG* g = G + (size_t)slot[s] * rows * n_R;
   const double inv = 1.0 / cscale[s];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < n_R; i += nw) {
+  for (int i = wid; i < rows; i += nw) {
     const TG* gi = g + (size_t)i * n_R;
     double v = 0;
     for (int k = lane; k < n_R; k += 32) v += (double)gi[k] * xs[k];
     v = warp_sum(v);
-    if (lane == 0) Y[(size_t)rdofs[i] * n_cells + s] = v * inv;
+    if (lane == 0) Y[out_row(i, n_R, rdofs, pdofs) * n_cells + s] = i < n_R ? v * inv : v;
   }
 }
 
-// few keys: segmented GEMM over 64 rows x 64 cells of one key, cells in key order (perm)
+// few keys: segmented GEMM over 64 rows x 64 cells of one key, cells in key order (perm);
+// FP32 operands accumulate in FP32 (TG = float), FP64 in FP64
 template <typename TG>
 __global__ void __launch_bounds__(256)
-    k_local_segmm(int n_cells, int n_R, const TG* __restrict__ G, const int* __restrict__ tile_seg,
+    k_local_segmm(int n_cells, int n_R, int n_P, const TG* __restrict__ G, const int* __restrict__ tile_seg,
                   const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
-                  const double* __restrict__ cscale, const int* __restrict__ rdofs, const double* __restrict__ X,
-                  double* __restrict__ Y) {
+                  const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
+                  const double* __restrict__ X, double* __restrict__ Y) {
   const int tile = blockIdx.x;
   const int k = tile_seg[tile];
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[k + 1];
+  const int rows = n_R + n_P;
   const int i0 = blockIdx.y * 64;
-  const TG* g = G + (size_t)k * n_R * n_R;
-  __shared__ double Gs[64][33];
-  __shared__ double Xs[32][65];
+  const TG* g = G + (size_t)k * rows * n_R;
+  __shared__ TG Gs[64][33];
+  __shared__ TG Xs[32][65];
   __shared__ int cells[64];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   if (threadIdx.x < 64) {
     const int c = c0 + threadIdx.x;
     cells[threadIdx.x] = c < c_end ? perm[c] : -1;
   }
-  double acc[4][4];
+  TG acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < 4; ++v) acc[u][v] = TG(0);
   for (int l0 = 0; l0 < n_R; l0 += 32) {
     __syncthreads();
     for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
       const int r = t / 32, c = t % 32;
       const int gi = i0 + r, gl = l0 + c;
-      Gs[r][c] = (gi < n_R && gl < n_R) ? (double)g[(size_t)gi * n_R + gl] : 0.0;
+      Gs[r][c] = (gi < rows && gl < n_R) ? g[(size_t)gi * n_R + gl] : TG(0);
     }
     for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
       const int r = t / 64, c = t % 64;
       const int gl = l0 + r, s = cells[c];
-      Xs[r][c] = (gl < n_R && s >= 0) ? X[(size_t)rdofs[gl] * n_cells + s] : 0.0;
+      Xs[r][c] = (gl < n_R && s >= 0) ? (TG)X[(size_t)rdofs[gl] * n_cells + s] : TG(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int l = 0; l < 32; ++l) {
-      double gv[4], xv[4];
+      TG gv[4], xv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) gv[u] = Gs[ty + 16 * u][l];
 #pragma unroll
@@ -594,22 +608,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int gi = i0 + ty + 16 * u;
-      if (gi < n_R) Y[(size_t)rdofs[gi] * n_cells + s] = acc[u][v] * inv;
+      if (gi < rows) Y[out_row(gi, n_R, rdofs, pdofs) * n_cells + s] = gi < n_R ? (double)acc[u][v] * inv
+                                                                            : (double)acc[u][v];
     }
   }
-}
-
-// tP at the corner rows of a local buffer:  buf[pdof_j, s] = sum_i Phi^{slot(s)}[i][j] x_R^s[i]
-__global__ void k_phi_t(int n_cells, int n_R, int n_P, const double* __restrict__ Phi, const int* __restrict__ slot,
-                        const int* __restrict__ rdofs, const int* __restrict__ pdofs, const double* __restrict__ X,
-                        double* __restrict__ buf) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (s >= n_cells) return;
-  const double* ph = Phi + (size_t)slot[s] * n_R * n_P;
-  double v = 0;
-  for (int i = 0; i < n_R; ++i) v += ph[(size_t)i * n_P + j] * X[(size_t)rdofs[i] * n_cells + s];
-  buf[(size_t)pdofs[j] * n_cells + s] = v;
 }
 
 // Y_R^s += Phi^{slot(s)} xP(corners of s)
@@ -702,17 +704,21 @@ struct SolverTmp {
 // ---------------------------------------------------------------------------------------------
 // preconditioner setup
 // ---------------------------------------------------------------------------------------------
-void gj_invert(lat_ctx* h, double* A, int n, int batch) {
+// invert `batch` n x n matrices stored with a stride of bs elements (in place)
+void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs) {
   DBuf<double> Pinv, Cbuf, Rbuf;
   Pinv.ensure((size_t)batch * GJB * GJB);
   Cbuf.ensure((size_t)batch * n * GJB);
   Rbuf.ensure((size_t)batch * GJB * n);
   for (int k0 = 0; k0 < n; k0 += GJB) {
     const int kw = std::min(GJB, n - k0);
-    k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p);
-    k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, k0, kw, A, Pinv.p, Rbuf.p);
-    k_gj_update<<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(n, k0, kw, A, Pinv.p,
-                                                                                   Cbuf.p, Rbuf.p);
+    k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p);
+    k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Rbuf.p);
+    {
+      KernelTimer kt(h, "gj_update");
+      k_gj_update<<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p,
+                                                                                     Cbuf.p, Rbuf.p);
+    }
     LAT_CHECK_LAUNCH();
   }
   LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -770,7 +776,8 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   h->max_tiles = (int)tseg.size();
   h->key_slot.upload(slot_cell, h->stream);  // slot of each cell
   // dense local blocks
-  const size_t gsz = (size_t)nk * nR * nR;
+  const int64_t gstride = (int64_t)(nR + nP) * nR;   // augmented [G; Phi^T] per key
+  const size_t gsz = (size_t)nk * gstride;
   h->G.ensure(gsz);
   h->KRP.ensure((size_t)nk * nR * nP);
   h->Sloc.ensure((size_t)nk * nP * nP);
@@ -792,7 +799,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
           nR, nP, h->G.p, h->KRP.p, h->Sloc.p);
     LAT_CHECK_LAUNCH();
   }
-  gj_invert(h, h->G.p, nR, nk);
+  gj_invert(h, h->G.p, nR, nk, gstride);
   k_phi<<<dim3(div_up(nR * nP, 128), nk), 128, 0, h->stream>>>(nR, nP, h->G.p, h->KRP.p, h->Phi.p);
   k_schur<<<nk, 64, 0, h->stream>>>(nR, nP, h->KRP.p, h->Phi.p, h->Sloc.p);
   LAT_CHECK_LAUNCH();
@@ -805,7 +812,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
     k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p, h->coarse_col.p,
         h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p);
     LAT_CHECK_LAUNCH();
-    gj_invert(h, h->CoarseInv.p, (int)np, 1);
+    gj_invert(h, h->CoarseInv.p, (int)np, 1, np * np);
   }
   int fl = 0;
   LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -859,38 +866,43 @@ void kinv(lat_ctx* h, const double* v, double* w) {
   const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
   const int64_t nloc = (int64_t)h->n_loc * ns;
   double* wl = loc_of(h, w);
-  LAT_CUDA(cudaMemsetAsync(wl, 0, nloc * sizeof(double), h->stream));
-  // y_R = G~ v_R
+  (void)nloc;
+  // every remaining and corner row of every cell is written below
+  // y_R = G~ v_R and Phi^T v_R (corner rows of wl) in one product
   const bool gemv = (int64_t)h->n_keys * 8 > ns;
   const bool lo = h->prec != LAT_FP64;
   if (gemv) {
+    KernelTimer kt(h, "local_gemv");
     const size_t shm = (size_t)nR * sizeof(double);
     if (lo) {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nR, h->G32.p, h->key_slot.p, h->c_cell.p, h->rdofs.p, v, wl);
+      k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G32.p, h->key_slot.p, h->c_cell.p,
+                                                       h->rdofs.p, h->pdofs.p, v, wl);
     } else {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, h->G.p, h->key_slot.p, h->c_cell.p, h->rdofs.p, v, wl);
+      k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G.p, h->key_slot.p, h->c_cell.p,
+                                                        h->rdofs.p, h->pdofs.p, v, wl);
     }
   } else {
-    dim3 grid(h->max_tiles, div_up(nR, 64));
+    KernelTimer kt(h, "local_segmm");
+    dim3 grid(h->max_tiles, div_up(nR + nP, 64));
     if (lo)
-      k_local_segmm<float><<<grid, 256, 0, h->stream>>>(ns, nR, h->G32.p, h->tile_seg.p, h->tile_c0.p,
-          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, v, wl);
+      k_local_segmm<float><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G32.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl);
     else
-      k_local_segmm<double><<<grid, 256, 0, h->stream>>>(ns, nR, h->G.p, h->tile_seg.p, h->tile_c0.p,
-          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, v, wl);
+      k_local_segmm<double><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl);
   }
   LAT_CHECK_LAUNCH();
   if (h->n_primal) {
-    // g_P = v_P + sum_s A_P^T Phi^T v_R   (corner rows of wl are free scratch here)
-    k_phi_t<<<dim3(div_up(ns, 128), nP), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
-                                                              h->pdofs.p, v, wl);
+    // g_P = v_P + sum_s A_P^T Phi^T v_R   (from the corner rows of wl)
     LAT_CUDA(cudaMemcpyAsync(h->gP.p, pr_of(h, v), h->n_primal * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
         h->p_copy.p, wl, h->gP.p, 1);
     k_gemv<<<div_up(h->n_primal * 32, 256), 256, 0, h->stream>>>(h->n_primal, h->CoarseInv.p, h->gP.p, pr_of(h, w));
-    k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl);
+  }
+  k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl);
+  if (h->n_primal) {
     k_phi_n<<<dim3(div_up(ns, 128), nR), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
                                                                h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl);
     LAT_CHECK_LAUNCH();
@@ -1047,6 +1059,7 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
       run_block_precond(h, vj, zj, o->pcg_iters);
       feti_operator(h, zj, w, true);
       // CGS with one re-orthogonalisation
+      KernelTimer kt(h, "krylov_orth");
       for (int pass = 0; pass < 2; ++pass) {
         k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, h->V.p, w, h->dots_part.p);
         k_multidot_final<<<j + 1, 256, 0, h->stream>>>(nb, h->dots_part.p, pass == 0 ? hcol : h2);

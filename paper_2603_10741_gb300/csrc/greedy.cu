@@ -198,6 +198,7 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
       k_g_select<<<1, 1024, 0, h->stream>>>(it, n_cols, limit, eps, h->g_inf.p, h->g_nrm2.p,
                                             h->g_state.p, h->S.p, h->g_maxres.p, h->g_scale.p);
       k_g_zeta<<<zgrid, 256, 0, h->stream>>>(it, n_rows, h->g_delta.p, h->g_state.p, h->g_scale.p, h->g_Z.p);
+      KernelTimer kt(h, "greedy_update");
       k_g_update<<<n_cols, kColThreads, 0, h->stream>>>(it, n_rows, n_cols, h->g_delta.p, h->g_Z.p,
                                                         h->g_state.p, h->g_beta.p, h->g_inf.p, h->g_nrm2.p);
     }

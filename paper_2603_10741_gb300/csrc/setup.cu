@@ -464,6 +464,12 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  for (auto& kv : h->ev)
+    for (auto& pr : kv.second) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return LAT_OK;
 }
@@ -572,5 +578,38 @@ extern "C" lat_status lattice_checkpoint_load(lat_handle h, const char* path, in
       else LAT_CUDA(cudaMemsetAsync(up, 0, h->n_dof * sizeof(double), h->stream));
     }
     LAT_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
+extern "C" lat_status lattice_set_timing(lat_handle h, int32_t enable) {
+  if (!h) return LAT_EINVAL;
+  return guard(h, [&] {
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    for (auto& kv : h->ev)
+      for (auto& pr : kv.second) {
+        h->ev_pool.push_back(pr.first);
+        h->ev_pool.push_back(pr.second);
+      }
+    h->ev.clear();
+    h->timing = enable != 0;
+  });
+}
+
+extern "C" lat_status lattice_kernel_time(lat_handle h, const char* name, double* total_ms, int32_t* launches) {
+  if (!h || !name || !total_ms || !launches) return LAT_EINVAL;
+  return guard(h, [&] {
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    double t = 0;
+    int n = 0;
+    auto it = h->ev.find(name);
+    if (it != h->ev.end())
+      for (auto& pr : it->second) {
+        float ms = 0;
+        LAT_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        t += ms;
+        ++n;
+      }
+    *total_ms = t;
+    *launches = n;
   });
 }

@@ -22,7 +22,8 @@ EXPORTS = ["lattice_setup", "lattice_destroy", "lattice_sizes", "lattice_last_er
            "lattice_set_mu_scale", "lattice_predictor", "lattice_gather", "assemble_residual_tangent",
            "greedy_select", "select_principal_cells", "apply_reduced_tangent", "lattice_default_opts",
            "newton_step", "adjoint_gradient", "feti_apply", "lattice_prepare_solver", "feti_to_global",
-           "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve"]
+           "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve",
+           "lattice_set_timing", "lattice_kernel_time"]
 
 
 class LatticeError(RuntimeError):
@@ -89,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         "feti_from_global": [P, P, P],
         "lattice_checkpoint_save": [P, C.c_char_p, I32, D, P, P],
         "lattice_checkpoint_load": [P, C.c_char_p, P, P, P, P],
+        "lattice_set_timing": [P, I32],
+        "lattice_kernel_time": [P, C.c_char_p, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -312,6 +315,15 @@ class Lattice:
         v = self.krylov_vector()
         self._check(self._lib.feti_from_global(self.h, _ptr(u), _ptr(v)))
         return v
+
+    def lattice_set_timing(self, enable=True):
+        self._check(self._lib.lattice_set_timing(self.h, int(enable)))
+
+    def lattice_kernel_time(self, name):
+        """(summed ms, launches) of a named kernel since lattice_set_timing."""
+        t, n = C.c_double(0), C.c_int32(0)
+        self._check(self._lib.lattice_kernel_time(self.h, name.encode(), C.byref(t), C.byref(n)))
+        return t.value, n.value
 
     def lattice_checkpoint_save(self, path, step, load, u, u_prev=None):
         self._check(self._lib.lattice_checkpoint_save(self.h, str(path).encode(), int(step), float(load),
