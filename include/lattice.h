@@ -153,8 +153,12 @@ typedef struct {
   double krylov_rtol;      /* FGMRES relative residual target */
   int32_t krylov_max_it;   /* total FGMRES iterations per solve */
   int32_t krylov_restart;
-  int32_t pcg_iters;       /* PCG iterations of the interface sub-preconditioner */
+  int32_t pcg_iters;       /* cap on PCG iterations of the interface sub-preconditioner */
   int32_t armijo_max_m;    /* backtracking cap */
+  double pcg_rtol;         /* interface PCG stops when sqrt(r^T M r / r0^T M r0) <= pcg_rtol
+                              (0: always pcg_iters iterations) */
+  int32_t interface_precond; /* M of the interface PCG: 0 Dirichlet B_D S_DD B_D^T with the local
+                                dual Schur complements of the principals, 1 lumped B_D K_DD B_D^T */
 } lat_newton_opts;
 
 typedef struct {
@@ -166,10 +170,12 @@ typedef struct {
   int32_t krylov_its_total;
   int32_t armijo_m_max;
   double t_residual_ms, t_select_ms, t_setup_ms, t_krylov_ms, t_linesearch_ms; /* phase times */
+  int32_t pcg_its_total;   /* interface PCG iterations inside the preconditioner */
 } lat_newton_report;
 
-/* Default options (eps 3e-4, max_nr 256, newton_rtol 1e-8, krylov_rtol 1e-10 for FP64 and 1e-6
- * for the mixed modes, restart 60, 5 PCG iterations, Armijo cap 30). */
+/* Default options (eps 3e-4 in 2D and 5e-3 in 3D, max_nr 256, newton_rtol 1e-8, krylov_rtol
+ * 1e-10 for FP64 and 1e-6 for the mixed modes, restart 60, interface PCG to 1e-2 with at most 100
+ * iterations, Armijo cap 30). */
 lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 
 /* Newton-Raphson for one load step (Section 2.2.5) from the initial guess in u_glob (dev,
@@ -218,6 +224,9 @@ lat_status feti_from_global(lat_handle h, const double* u_glob, double* v);
  * ms) and the launch count of one name since then. */
 lat_status lattice_set_timing(lat_handle h, int32_t enable);
 lat_status lattice_kernel_time(lat_handle h, const char* name, double* total_ms, int32_t* launches);
+
+/* Number of kernels launched through this handle since it was created. */
+lat_status lattice_launch_count(lat_handle h, int64_t* launches);
 
 /* Load-step checkpoint: the step index, the load parameter and the last two converged states
  * (dev [n_dof]; u_prev may be NULL) to/from a binary file. */

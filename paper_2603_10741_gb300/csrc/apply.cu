@@ -130,10 +130,10 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
   dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
   if (h->force_all) {
     KernelTimer kt(h, "apply_percell");
-    k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y);
+    LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
   } else {
     KernelTimer kt(h, "apply_reduced");
-    k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y);
+    LAT_LAUNCH(h, k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
   }
   LAT_CHECK_LAUNCH();
 }

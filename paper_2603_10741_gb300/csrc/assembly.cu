@@ -422,21 +422,21 @@ void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_g
   auto ct = colors(h);
   KernelTimer kt(h, "residual");
   if (h->dim == 2) {
-    k_residual<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
-        h->cell_nodes.p, h->mu_cell.p, -1.0, h->lam, u_glob, f_cells, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_residual<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
+        h->cell_nodes.p, h->mu_cell.p, -1.0, h->lam, u_glob, f_cells, h->minJ_cell.p));
   } else {
     LAT_CUDA(cudaFuncSetAttribute(k_residual<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_residual<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
-        h->cell_nodes.p, h->mu_cell.p, -1.0, h->lam, u_glob, f_cells, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_residual<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
+        h->cell_nodes.p, h->mu_cell.p, -1.0, h->lam, u_glob, f_cells, h->minJ_cell.p));
   }
   LAT_CHECK_LAUNCH();
   if (r_glob) {
-    k_scatter<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim,
-        h->n_nodes_cell, h->n_cells, h->copy_ptr.p, h->copy_idx.p, f_cells, r_glob);
+    LAT_LAUNCH(h, k_scatter<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim,
+        h->n_nodes_cell, h->n_cells, h->copy_ptr.p, h->copy_idx.p, f_cells, r_glob));
     LAT_CHECK_LAUNCH();
   }
   double* sc = scratch_scalars(h);
-  k_min_reduce<<<1, 1024, 0, h->stream>>>(h->n_cells, h->minJ_cell.p, sc);
+  LAT_LAUNCH(h, k_min_reduce<<<1, 1024, 0, h->stream>>>(h->n_cells, h->minJ_cell.p, sc));
   LAT_CHECK_LAUNCH();
   LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -454,17 +454,17 @@ void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, i
   auto ct = colors(h);
   KernelTimer kt(h, quad ? "tangent_reduced" : "tangent_full");
   if (h->dim == 2) {
-    k_tangent<2><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
-        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_tangent<2><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
+        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p));
   } else {
     LAT_CUDA(cudaFuncSetAttribute(k_tangent<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_tangent<3><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
-        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_tangent<3><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
+        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p));
   }
   LAT_CHECK_LAUNCH();
   if (negJ) {
     double* sc = scratch_scalars(h);
-    k_min_reduce<<<1, 1024, 0, h->stream>>>(n_sel, h->minJ_cell.p, sc);
+    LAT_LAUNCH(h, k_min_reduce<<<1, 1024, 0, h->stream>>>(n_sel, h->minJ_cell.p, sc));
     LAT_CHECK_LAUNCH();
     LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -478,16 +478,16 @@ void run_tangent_apply_exact(lat_ctx* h, const double* u_glob, const double* v_g
   auto g = geom(h, 0);
   auto ct = colors(h);
   if (h->dim == 2) {
-    k_tangent_apply<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g,
-        ct, h->cell_nodes.p, h->mu_cell.p, h->lam, u_glob, v_glob, h->f_cells.p);
+    LAT_LAUNCH(h, k_tangent_apply<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g,
+        ct, h->cell_nodes.p, h->mu_cell.p, h->lam, u_glob, v_glob, h->f_cells.p));
   } else {
     LAT_CUDA(cudaFuncSetAttribute(k_tangent_apply<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_tangent_apply<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g,
-        ct, h->cell_nodes.p, h->mu_cell.p, h->lam, u_glob, v_glob, h->f_cells.p);
+    LAT_LAUNCH(h, k_tangent_apply<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g,
+        ct, h->cell_nodes.p, h->mu_cell.p, h->lam, u_glob, v_glob, h->f_cells.p));
   }
   LAT_CHECK_LAUNCH();
-  k_scatter<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim,
-      h->n_nodes_cell, h->n_cells, h->copy_ptr.p, h->copy_idx.p, h->f_cells.p, y_glob);
+  LAT_LAUNCH(h, k_scatter<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim,
+      h->n_nodes_cell, h->n_cells, h->copy_ptr.p, h->copy_idx.p, h->f_cells.p, y_glob));
   LAT_CHECK_LAUNCH();
 }
 
@@ -499,23 +499,23 @@ void run_grad_mu(lat_ctx* h, const double* u_glob, const double* w_glob, double*
   auto g = geom(h, 0);
   auto ct = colors(h);
   if (h->dim == 2) {
-    k_residual<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
-        h->cell_nodes.p, h->mu_cell.p, h->mu, 0.0, u_glob, h->f_cells.p, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_residual<2><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
+        h->cell_nodes.p, h->mu_cell.p, h->mu, 0.0, u_glob, h->f_cells.p, h->minJ_cell.p));
   } else {
     LAT_CUDA(cudaFuncSetAttribute(k_residual<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    k_residual<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
-        h->cell_nodes.p, h->mu_cell.p, h->mu, 0.0, u_glob, h->f_cells.p, h->minJ_cell.p);
+    LAT_LAUNCH(h, k_residual<3><<<h->n_cells, kCellThreads, shm, h->stream>>>(h->n_cells, h->n_nodes_cell, g, ct,
+        h->cell_nodes.p, h->mu_cell.p, h->mu, 0.0, u_glob, h->f_cells.p, h->minJ_cell.p));
   }
   LAT_CHECK_LAUNCH();
-  k_cell_dot<<<h->n_cells, 256, 0, h->stream>>>(h->n_cells, h->n_loc, w_glob, h->cell_nodes.p,
-      h->n_nodes_cell, h->dim, h->f_cells.p, grad);
+  LAT_LAUNCH(h, k_cell_dot<<<h->n_cells, 256, 0, h->stream>>>(h->n_cells, h->n_loc, w_glob, h->cell_nodes.p,
+      h->n_nodes_cell, h->dim, h->f_cells.p, grad));
   LAT_CHECK_LAUNCH();
 }
 
 double run_norm_free(lat_ctx* h, const double* r) {
   double* sc = scratch_scalars(h);
-  k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 0, sc + 16);
-  k_final_sum<<<1, 512, 0, h->stream>>>(kRedBlocks, sc + 16, sc);
+  LAT_LAUNCH(h, k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 0, sc + 16));
+  LAT_LAUNCH(h, k_final_sum<<<1, 512, 0, h->stream>>>(kRedBlocks, sc + 16, sc));
   LAT_CHECK_LAUNCH();
   LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -524,9 +524,9 @@ double run_norm_free(lat_ctx* h, const double* r) {
 
 double run_norm_all(lat_ctx* h, const double* r) {
   double* sc = scratch_scalars(h);
-  k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 0, sc + 16);
-  k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 1, sc + 16 + kRedBlocks);
-  k_final_sum<<<1, 512, 0, h->stream>>>(2 * kRedBlocks, sc + 16, sc);
+  LAT_LAUNCH(h, k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 0, sc + 16));
+  LAT_LAUNCH(h, k_sumsq_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, r, h->dof_fixed.p, 1, sc + 16 + kRedBlocks));
+  LAT_LAUNCH(h, k_final_sum<<<1, 512, 0, h->stream>>>(2 * kRedBlocks, sc + 16, sc));
   LAT_CHECK_LAUNCH();
   LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -535,8 +535,8 @@ double run_norm_all(lat_ctx* h, const double* r) {
 
 double run_dot_fixed(lat_ctx* h, const double* a, const double* b) {
   double* sc = scratch_scalars(h);
-  k_dot_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, a, b, h->dof_fixed.p, sc + 16);
-  k_final_sum<<<1, 512, 0, h->stream>>>(kRedBlocks, sc + 16, sc);
+  LAT_LAUNCH(h, k_dot_masked<<<kRedBlocks, 256, 0, h->stream>>>(h->n_dof, a, b, h->dof_fixed.p, sc + 16));
+  LAT_LAUNCH(h, k_final_sum<<<1, 512, 0, h->stream>>>(kRedBlocks, sc + 16, sc));
   LAT_CHECK_LAUNCH();
   LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));

@@ -30,6 +30,13 @@ struct LatError {
 
 #define LAT_CHECK_LAUNCH() LAT_CUDA(cudaGetLastError())
 
+// every kernel launch of the library goes through this wrapper, which counts it on the handle
+#define LAT_LAUNCH(h, ...)   \
+  do {                       \
+    ++(h)->n_launch;         \
+    __VA_ARGS__;             \
+  } while (0)
+
 #define LAT_REQUIRE(cond, code, text)                                                      \
   do {                                                                                     \
     if (!(cond)) throw LatError{code, text};                                               \
@@ -99,6 +106,7 @@ struct lat_ctx {
 
   // FETI-DP structure
   int n_P = 0, n_R = 0;               // local primal (corner) / remaining dofs
+  int n_I = 0;                        // interior dofs: rdofs[0, n_I); dual dofs follow
   DBuf<int> corner_of_node;           // [n_nodes_cell] corner id or -1
   DBuf<int> rdofs, pdofs;             // [n_R], [n_P] local dof ids
   DBuf<int> rpos;                     // [n_loc] position in rdofs or -1
@@ -138,6 +146,8 @@ struct lat_ctx {
   DBuf<double> delta_cell, c_cell;    // per-cell inverse weight and scale
   DBuf<double> G, Phi, Sloc;          // [n_keys][n_R][n_R], [n_keys][n_R][n_P], [n_keys][n_P][n_P]
   DBuf<float> G32;
+  DBuf<double> SDD;                   // [n_keys][n_D][n_D] dual Schur complements
+  DBuf<float> SDD32;
   DBuf<__nv_bfloat16> G16;
   DBuf<double> KRP, Coarse, CoarseInv;
   DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
@@ -148,6 +158,9 @@ struct lat_ctx {
   DBuf<double> red_part;            // reduction scratch
   int max_tiles = 0;
   bool indefinite = false;
+  int64_t pcg_its_total = 0;
+  int64_t n_launch = 0;
+  int iface = 0;                      // interface preconditioner: 0 Dirichlet, 1 lumped               // kernels launched through this handle          // interface PCG iterations since the last reset
   bool verbose = false;               // LATTICE_VERBOSE=1: per-iteration log on stderr           // some local or coarse pivot was negative
   double *h_pinned = nullptr;          // small pinned host scratch
 
@@ -310,7 +323,7 @@ void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, 
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
 void run_feti_operator(lat_ctx* h, const double* v, double* w);
 void run_kinv(lat_ctx* h, const double* v, double* w);
-void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters);
+void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, double pcg_rtol);
 int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o, double* rel_out);
 void run_feti_to_global(lat_ctx* h, const double* v, double* u);
 void run_feti_from_global(lat_ctx* h, const double* u, double* v, bool split);

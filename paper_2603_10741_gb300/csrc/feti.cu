@@ -459,6 +459,16 @@ __global__ void __launch_bounds__(256) k_gj_update(int n, int64_t bs, int k0, in
   }
 }
 
+// trailing block of a partly swept matrix: snap[b][i][j] = A[split + i][split + j]
+__global__ void k_gj_snapshot(int n, int64_t bs, int split, const double* __restrict__ A, double* __restrict__ snap) {
+  const int b = blockIdx.y;
+  const int m = n - split;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)m * m) return;
+  const int i = (int)(t / m), j = (int)(t % m);
+  snap[(size_t)b * m * m + t] = A[(size_t)b * bs + (size_t)(split + i) * n + split + j];
+}
+
 // Phi = -G K_RP [k][n_R][n_P]; Phi^T is also stored as rows n_R.. of the augmented local
 // matrix [G; Phi^T] ((n_R + n_P) x n_R per key), so that one GEMM gives G x and Phi^T x
 __global__ void k_phi(int n_R, int n_P, double* __restrict__ G, const double* __restrict__ KRP,
@@ -546,14 +556,16 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// few keys: segmented GEMM over 64 rows x 64 cells of one key, cells in key order (perm);
-// FP32 operands accumulate in FP32 (TG = float), FP64 in FP64
-template <typename TG>
+// few keys: segmented GEMM over 64 rows x BN cells of one key, cells in key order (perm);
+// FP32 operands accumulate in FP32 (TG = float), FP64 in FP64.  BN = 16 for FP64 (ALU bound:
+// narrow tiles waste few multiply-adds on short segments), 64 for FP32.
+template <typename TG, int BN>
 __global__ void __launch_bounds__(256)
     k_local_segmm(int n_cells, int n_R, int n_P, const TG* __restrict__ G, const int* __restrict__ tile_seg,
                   const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                   const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
                   const double* __restrict__ X, double* __restrict__ Y) {
+  constexpr int NV = BN / 16;
   const int tile = blockIdx.x;
   const int k = tile_seg[tile];
   const int c0 = tile_c0[tile];
@@ -562,18 +574,18 @@ __global__ void __launch_bounds__(256)
   const int i0 = blockIdx.y * 64;
   const TG* g = G + (size_t)k * rows * n_R;
   __shared__ TG Gs[64][33];
-  __shared__ TG Xs[32][65];
-  __shared__ int cells[64];
+  __shared__ TG Xs[32][BN + 1];
+  __shared__ int cells[BN];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  if (threadIdx.x < 64) {
+  if (threadIdx.x < BN) {
     const int c = c0 + threadIdx.x;
     cells[threadIdx.x] = c < c_end ? perm[c] : -1;
   }
-  TG acc[4][4];
+  TG acc[4][NV];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = TG(0);
+    for (int v = 0; v < NV; ++v) acc[u][v] = TG(0);
   for (int l0 = 0; l0 < n_R; l0 += 32) {
     __syncthreads();
     for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
@@ -581,27 +593,27 @@ __global__ void __launch_bounds__(256)
       const int gi = i0 + r, gl = l0 + c;
       Gs[r][c] = (gi < rows && gl < n_R) ? g[(size_t)gi * n_R + gl] : TG(0);
     }
-    for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
-      const int r = t / 64, c = t % 64;
+    for (int t = threadIdx.x; t < 32 * BN; t += blockDim.x) {
+      const int r = t / BN, c = t % BN;
       const int gl = l0 + r, s = cells[c];
       Xs[r][c] = (gl < n_R && s >= 0) ? (TG)X[(size_t)rdofs[gl] * n_cells + s] : TG(0);
     }
     __syncthreads();
 #pragma unroll 8
     for (int l = 0; l < 32; ++l) {
-      TG gv[4], xv[4];
+      TG gv[4], xv[NV];
 #pragma unroll
       for (int u = 0; u < 4; ++u) gv[u] = Gs[ty + 16 * u][l];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) xv[v] = Xs[l][tx + 16 * v];
+      for (int v = 0; v < NV; ++v) xv[v] = Xs[l][tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(gv[u], xv[v], acc[u][v]);
+        for (int v = 0; v < NV; ++v) acc[u][v] = fma(gv[u], xv[v], acc[u][v]);
     }
   }
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < NV; ++v) {
     const int s = cells[tx + 16 * v];
     if (s < 0) continue;
     const double inv = 1.0 / cscale[s];
@@ -611,6 +623,29 @@ __global__ void __launch_bounds__(256)
       if (gi < rows) Y[out_row(gi, n_R, rdofs, pdofs) * n_cells + s] = gi < n_R ? (double)acc[u][v] * inv
                                                                             : (double)acc[u][v];
     }
+  }
+}
+
+// Dirichlet interface preconditioner, local part: y_D = c_s S_DD^{slot(s)} x_D on the dual rows
+// (S_DD = K_DD - K_DI K_II^{-1} K_ID of the cell's principal, one CTA per cell, warp per row)
+template <typename TS>
+__global__ void __launch_bounds__(256)
+    k_dual_schur(int n_cells, int n_I, int n_D, const TS* __restrict__ SDD, const int* __restrict__ slot,
+                 const double* __restrict__ cscale, const int* __restrict__ rdofs, const double* __restrict__ X,
+                 double* __restrict__ Y) {
+  extern __shared__ double xs[];
+  const int s = blockIdx.x;
+  for (int k = threadIdx.x; k < n_D; k += blockDim.x) xs[k] = X[(size_t)rdofs[n_I + k] * n_cells + s];
+  __syncthreads();
+  const TS* S = SDD + (size_t)slot[s] * n_D * n_D;
+  const double c = cscale[s];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = wid; i < n_D; i += nw) {
+    const TS* si = S + (size_t)i * n_D;
+    double v = 0;
+    for (int k = lane; k < n_D; k += 32) v += (double)si[k] * xs[k];
+    v = warp_sum(v);
+    if (lane == 0) Y[(size_t)rdofs[n_I + i] * n_cells + s] = c * v;
   }
 }
 
@@ -685,6 +720,9 @@ __global__ void k_gmres_solve(int k, int m, const double* __restrict__ H, const 
   }
 }
 
+// cells per segmented-GEMM tile: 16 in FP64, 64 in the mixed modes
+int seg_bn(lat_ctx* h) { return h->prec == LAT_FP64 ? 16 : 64; }
+
 int red_blocks(int64_t n) { return (int)std::min<int64_t>(kRed, std::max<int64_t>(1, (n + 255) / 256)); }
 int ew_blocks(lat_ctx* h, int64_t n) {
   return (int)std::min<int64_t>((int64_t)h->n_sm * 8, std::max<int64_t>(1, (n + 255) / 256));
@@ -693,8 +731,8 @@ int ew_blocks(lat_ctx* h, int64_t n) {
 // device dot -> out[0] (no host sync)
 void dev_dot(lat_ctx* h, int64_t n, const double* a, const double* b, double* out) {
   const int nb = red_blocks(n);
-  k_dot_part<<<nb, 256, 0, h->stream>>>(n, a, b, h->red_part.p + 1024);
-  k_sum_part<<<1, 512, 0, h->stream>>>(nb, h->red_part.p + 1024, out);
+  LAT_LAUNCH(h, k_dot_part<<<nb, 256, 0, h->stream>>>(n, a, b, h->red_part.p + 1024));
+  LAT_LAUNCH(h, k_sum_part<<<1, 512, 0, h->stream>>>(nb, h->red_part.p + 1024, out));
 }
 
 struct SolverTmp {
@@ -704,22 +742,36 @@ struct SolverTmp {
 // ---------------------------------------------------------------------------------------------
 // preconditioner setup
 // ---------------------------------------------------------------------------------------------
-// invert `batch` n x n matrices stored with a stride of bs elements (in place)
-void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs) {
+// invert `batch` n x n matrices stored with a stride of bs elements (in place).  With split in
+// (0, n) the pivot blocks stop at `split` once: the trailing block [split, n)^2 then holds the
+// Schur complement A_22 - A_21 A_11^{-1} A_12, copied to snap ([batch][n-split]^2) before the
+// sweep continues.
+void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int split = -1, double* snap = nullptr) {
   DBuf<double> Pinv, Cbuf, Rbuf;
   Pinv.ensure((size_t)batch * GJB * GJB);
   Cbuf.ensure((size_t)batch * n * GJB);
   Rbuf.ensure((size_t)batch * GJB * n);
-  for (int k0 = 0; k0 < n; k0 += GJB) {
-    const int kw = std::min(GJB, n - k0);
-    k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p);
-    k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Rbuf.p);
+  if (snap && split == 0) {
+    LAT_LAUNCH(h, k_gj_snapshot<<<dim3(div_up((int64_t)n * n, 256), batch), 256, 0, h->stream>>>(n, bs, 0, A, snap));
+    LAT_CHECK_LAUNCH();
+  }
+  for (int k0 = 0; k0 < n;) {
+    int kw = std::min(GJB, n - k0);
+    if (split > 0 && k0 < split) kw = std::min(kw, split - k0);
+    LAT_LAUNCH(h, k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p));
+    LAT_LAUNCH(h, k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Rbuf.p));
     {
       KernelTimer kt(h, "gj_update");
-      k_gj_update<<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p,
-                                                                                     Cbuf.p, Rbuf.p);
+      LAT_LAUNCH(h, k_gj_update<<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p,
+                                                                                     Cbuf.p, Rbuf.p));
     }
     LAT_CHECK_LAUNCH();
+    k0 += kw;
+    if (snap && k0 == split) {
+      const int m = n - split;
+      LAT_LAUNCH(h, k_gj_snapshot<<<dim3(div_up((int64_t)m * m, 256), batch), 256, 0, h->stream>>>(n, bs, split, A, snap));
+      LAT_CHECK_LAUNCH();
+    }
   }
   LAT_CUDA(cudaStreamSynchronize(h->stream));
   Pinv.release();
@@ -739,8 +791,8 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   // keys and scales
   h->key_of_cell.ensure(ns);
   h->c_cell.ensure(ns);
-  k_cell_keys<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, h->n_r, h->force_all ? 1 : 0, h->alpha.p,
-                                                      h->cell_class.p, h->n_classes, h->key_of_cell.p, h->c_cell.p);
+  LAT_LAUNCH(h, k_cell_keys<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, h->n_r, h->force_all ? 1 : 0, h->alpha.p,
+                                                      h->cell_class.p, h->n_classes, h->key_of_cell.p, h->c_cell.p));
   LAT_CHECK_LAUNCH();
   std::vector<int> keys(ns);
   LAT_CUDA(cudaMemcpyAsync(keys.data(), h->key_of_cell.p, ns * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -763,7 +815,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   for (int s = 0; s < ns; ++s) perm[fill[slot_cell[s]]++] = s;
   std::vector<int> tseg, tc0;
   for (int k = 0; k < nk; ++k)
-    for (int c = cnt[k]; c < cnt[k + 1]; c += 64) {
+    for (int c = cnt[k]; c < cnt[k + 1]; c += seg_bn(h)) {
       tseg.push_back(k);
       tc0.push_back(c);
     }
@@ -790,18 +842,21 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   {
     dim3 grid(div_up(h->n_nodes_cell, 128), nk);
     if (h->dim == 2)
-      k_densify<2><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
+      LAT_LAUNCH(h, k_densify<2><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
           h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
-          nR, nP, h->G.p, h->KRP.p, h->Sloc.p);
+          nR, nP, h->G.p, h->KRP.p, h->Sloc.p));
     else
-      k_densify<3><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
+      LAT_LAUNCH(h, k_densify<3><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
           h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
-          nR, nP, h->G.p, h->KRP.p, h->Sloc.p);
+          nR, nP, h->G.p, h->KRP.p, h->Sloc.p));
     LAT_CHECK_LAUNCH();
   }
-  gj_invert(h, h->G.p, nR, nk, gstride);
-  k_phi<<<dim3(div_up(nR * nP, 128), nk), 128, 0, h->stream>>>(nR, nP, h->G.p, h->KRP.p, h->Phi.p);
-  k_schur<<<nk, 64, 0, h->stream>>>(nR, nP, h->KRP.p, h->Phi.p, h->Sloc.p);
+  const int nD = nR - h->n_I;
+  h->SDD.ensure((size_t)nk * nD * nD);
+  gj_invert(h, h->G.p, nR, nk, gstride, h->n_I, h->SDD.p);
+  h->iface = o ? o->interface_precond : 0;
+  LAT_LAUNCH(h, k_phi<<<dim3(div_up(nR * nP, 128), nk), 128, 0, h->stream>>>(nR, nP, h->G.p, h->KRP.p, h->Phi.p));
+  LAT_LAUNCH(h, k_schur<<<nk, 64, 0, h->stream>>>(nR, nP, h->KRP.p, h->Phi.p, h->Sloc.p));
   LAT_CHECK_LAUNCH();
   // coarse matrix, FP64, explicit inverse
   const int64_t np = h->n_primal;
@@ -809,8 +864,8 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
     h->CoarseInv.ensure((size_t)np * np);
     LAT_CUDA(cudaMemsetAsync(h->CoarseInv.p, 0, (size_t)np * np * sizeof(double), h->stream));
     const int64_t n_ent = (int64_t)h->coarse_row.n;
-    k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p, h->coarse_col.p,
-        h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p);
+    LAT_LAUNCH(h, k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p, h->coarse_col.p,
+        h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p));
     LAT_CHECK_LAUNCH();
     gj_invert(h, h->CoarseInv.p, (int)np, 1, np * np);
   }
@@ -822,7 +877,10 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   h->indefinite = (fl & 2) != 0;
   if (h->prec != LAT_FP64) {
     h->G32.ensure(gsz);
-    k_d2f<<<ew_blocks(h, gsz), 256, 0, h->stream>>>(gsz, h->G.p, h->G32.p);
+    LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, gsz), 256, 0, h->stream>>>(gsz, h->G.p, h->G32.p));
+    const size_t dsz = (size_t)nk * nD * nD;
+    h->SDD32.ensure(dsz);
+    LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, dsz), 256, 0, h->stream>>>(dsz, h->SDD.p, h->SDD32.p));
     LAT_CHECK_LAUNCH();
   }
   // temporaries
@@ -848,15 +906,15 @@ void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda) {
   run_apply(h, v, w, 0, vP, true);
   // primal rows -> assembled primal part, then clear corner rows
   if (h->n_primal)
-    k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
-        h->p_copy.p, w, pr_of(h, w), 0);
-  k_zero_rows<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->n_P, h->pdofs.p, w);
+    LAT_LAUNCH(h, k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
+        h->p_copy.p, w, pr_of(h, w), 0));
+  LAT_LAUNCH(h, k_zero_rows<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->n_P, h->pdofs.p, w));
   if (h->n_lambda) {
     if (with_lambda)
-      k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-          h->dual_l2.p, nullptr, la_of(h, v), 1.0, w);
-    k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, v, 1.0,
-                                                              la_of(h, w), 0);
+      LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+          h->dual_l2.p, nullptr, la_of(h, v), 1.0, w));
+    LAT_LAUNCH(h, k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, v, 1.0,
+                                                              la_of(h, w), 0));
   }
   LAT_CHECK_LAUNCH();
 }
@@ -876,35 +934,35 @@ void kinv(lat_ctx* h, const double* v, double* w) {
     const size_t shm = (size_t)nR * sizeof(double);
     if (lo) {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G32.p, h->key_slot.p, h->c_cell.p,
-                                                       h->rdofs.p, h->pdofs.p, v, wl);
+      LAT_LAUNCH(h, k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G32.p, h->key_slot.p, h->c_cell.p,
+                                                       h->rdofs.p, h->pdofs.p, v, wl));
     } else {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G.p, h->key_slot.p, h->c_cell.p,
-                                                        h->rdofs.p, h->pdofs.p, v, wl);
+      LAT_LAUNCH(h, k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G.p, h->key_slot.p, h->c_cell.p,
+                                                        h->rdofs.p, h->pdofs.p, v, wl));
     }
   } else {
     KernelTimer kt(h, "local_segmm");
     dim3 grid(h->max_tiles, div_up(nR + nP, 64));
     if (lo)
-      k_local_segmm<float><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G32.p, h->tile_seg.p, h->tile_c0.p,
-          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl);
+      LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G32.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl));
     else
-      k_local_segmm<double><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G.p, h->tile_seg.p, h->tile_c0.p,
-          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl);
+      LAT_LAUNCH(h, k_local_segmm<double, 16><<<grid, 256, 0, h->stream>>>(ns, nR, nP, h->G.p, h->tile_seg.p, h->tile_c0.p,
+          h->seg_ptr.p, h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p, v, wl));
   }
   LAT_CHECK_LAUNCH();
   if (h->n_primal) {
     // g_P = v_P + sum_s A_P^T Phi^T v_R   (from the corner rows of wl)
     LAT_CUDA(cudaMemcpyAsync(h->gP.p, pr_of(h, v), h->n_primal * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
-        h->p_copy.p, wl, h->gP.p, 1);
-    k_gemv<<<div_up(h->n_primal * 32, 256), 256, 0, h->stream>>>(h->n_primal, h->CoarseInv.p, h->gP.p, pr_of(h, w));
+    LAT_LAUNCH(h, k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
+        h->p_copy.p, wl, h->gP.p, 1));
+    LAT_LAUNCH(h, k_gemv<<<div_up(h->n_primal * 32, 256), 256, 0, h->stream>>>(h->n_primal, h->CoarseInv.p, h->gP.p, pr_of(h, w)));
   }
-  k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl);
+  LAT_LAUNCH(h, k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl));
   if (h->n_primal) {
-    k_phi_n<<<dim3(div_up(ns, 128), nR), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
-                                                               h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl);
+    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nR), 128, 0, h->stream>>>(ns, nR, nP, h->Phi.p, h->key_slot.p, h->rdofs.p,
+                                                               h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl));
     LAT_CHECK_LAUNCH();
   }
 }
@@ -913,11 +971,11 @@ void kinv(lat_ctx* h, const double* v, double* w) {
 void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
   LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
-  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, nullptr, p, 1.0, t1);
+  LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, nullptr, p, 1.0, t1));
   LAT_CHECK_LAUNCH();
   kinv(h, t1, t2);
-  k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, 1.0, q, 0);
+  LAT_LAUNCH(h, k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, 1.0, q, 0));
   LAT_CHECK_LAUNCH();
 }
 
@@ -925,20 +983,33 @@ void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
 void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2, double* wloc) {
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
   LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
-  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, h->dual_scale.p, r, 1.0, t1);
+  LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, h->dual_scale.p, r, 1.0, t1));
   LAT_CHECK_LAUNCH();
-  // K~ on the dual-only local vector (corners zero: primal part of t1 is zero)
-  if (h->prec == LAT_FP64) {
+  if (h->iface == 0) {
+    // Dirichlet: local dual Schur complements of the cells' principals
+    const int nD = h->n_R - h->n_I;
+    const size_t shm = (size_t)nD * sizeof(double);
+    if (h->prec == LAT_FP64) {
+      LAT_CUDA(cudaFuncSetAttribute(k_dual_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      LAT_LAUNCH(h, k_dual_schur<double><<<h->n_cells, 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD.p,
+          h->key_slot.p, h->c_cell.p, h->rdofs.p, t1, t2));
+    } else {
+      LAT_CUDA(cudaFuncSetAttribute(k_dual_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      LAT_LAUNCH(h, k_dual_schur<float><<<h->n_cells, 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD32.p,
+          h->key_slot.p, h->c_cell.p, h->rdofs.p, t1, t2));
+    }
+  } else if (h->prec == LAT_FP64) {
+    // lumped: K~ on the dual-only local vector (corners zero: primal part of t1 is zero)
     run_apply(h, t1, t2, 0, pr_of(h, t1), true);
   } else {
     h->x32.ensure(nloc);
     h->y32.ensure(nloc);
-    k_d2f<<<ew_blocks(h, nloc), 256, 0, h->stream>>>(nloc, t1, h->x32.p);
+    LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, nloc), 256, 0, h->stream>>>(nloc, t1, h->x32.p));
     run_apply(h, h->x32.p, h->y32.p, 1, pr_of(h, t1), true);
     run_f2d(h, nloc, h->y32.p, t2);
   }
-  k_jump_scaled<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, wloc, z);
+  LAT_LAUNCH(h, k_jump_scaled<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, wloc, z));
   LAT_CHECK_LAUNCH();
 }
 
@@ -953,7 +1024,7 @@ void run_kinv(lat_ctx* h, const double* v, double* w) {
                              h->stream));
 }
 
-void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters) {
+void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, double pcg_rtol) {
   const int64_t L = h->n_lambda;
   double* t = h->kv_tmp[2].p;   // K^-rom v_u, later v_u - B^T z
   double* t1 = h->kv_tmp[3].p;
@@ -973,41 +1044,58 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters) {
   LAT_REQUIRE(5 * L <= h->n_krylov, LAT_EINVAL, "multiplier work space too small");
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
   LAT_CUDA(cudaMemsetAsync(wloc, 0, nloc * sizeof(double), h->stream));
-  k_fill_dual_weights<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_scale.p, wloc);
+  LAT_LAUNCH(h, k_fill_dual_weights<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_scale.p, wloc));
   // y = v_l - B t
   LAT_CUDA(cudaMemcpyAsync(y, la_of(h, v), L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  k_jump<<<div_up(L, 256), 256, 0, h->stream>>>(L, h->lam_p.p, h->lam_m.p, t, -1.0, y, 1);
+  LAT_LAUNCH(h, k_jump<<<div_up(L, 256), 256, 0, h->stream>>>(L, h->lam_p.p, h->lam_m.p, t, -1.0, y, 1));
   LAT_CHECK_LAUNCH();
   // PCG on S x = y from x = 0
   LAT_CUDA(cudaMemsetAsync(x, 0, L * sizeof(double), h->stream));
   double* sc = h->red_part.p + 3000;  // see k_pcg_alpha
   if (pcg_iters > 0) {
+    // PCG until the preconditioned residual r^T M r has dropped by pcg_rtol^2 (checked on the
+    // host after every iteration), at most pcg_iters iterations, or until breakdown
     LAT_CUDA(cudaMemsetAsync(sc, 0, 8 * sizeof(double), h->stream));
     dual_precond(h, y, z, t1, t2, wloc);
     LAT_CUDA(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     dev_dot(h, L, y, z, sc);
+    double rz0 = -1.0;
+    if (pcg_rtol > 0) {
+      LAT_CUDA(cudaMemcpyAsync(h->h_pinned + 8, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LAT_CUDA(cudaStreamSynchronize(h->stream));
+      rz0 = h->h_pinned[8];
+    }
     const int nb = ew_blocks(h, L);
-    for (int it = 0; it < pcg_iters; ++it) {
+    int it = 0;
+    for (; it < pcg_iters; ++it) {
       dual_op(h, p, q, t1, t2);
       dev_dot(h, L, p, q, sc + 1);
-      k_pcg_alpha<<<1, 1, 0, h->stream>>>(sc);
-      k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, 1.0, p, x);
+      LAT_LAUNCH(h, k_pcg_alpha<<<1, 1, 0, h->stream>>>(sc));
+      LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, 1.0, p, x));
       if (it + 1 == pcg_iters) break;
-      k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, -1.0, q, y);
+      LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, -1.0, q, y));
       dual_precond(h, y, z, t1, t2, wloc);
       dev_dot(h, L, y, z, sc + 2);
-      k_pcg_beta<<<1, 1, 0, h->stream>>>(sc);
-      k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p);
+      LAT_LAUNCH(h, k_pcg_beta<<<1, 1, 0, h->stream>>>(sc));
+      LAT_CHECK_LAUNCH();
+      if (pcg_rtol > 0) {
+        LAT_CUDA(cudaMemcpyAsync(h->h_pinned + 8, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        LAT_CUDA(cudaStreamSynchronize(h->stream));
+        const double rz = h->h_pinned[8], frozen = h->h_pinned[13];
+        if (frozen != 0.0 || !(rz0 > 0) || rz <= pcg_rtol * pcg_rtol * rz0) break;
+      }
+      LAT_LAUNCH(h, k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p));
       LAT_CHECK_LAUNCH();
     }
+    h->pcg_its_total += it + 1;
   }
   // z_l = -x ;  w_u = K^-rom (v_u - B^T z_l) = K^-rom (v_u + B^T x)
   LAT_CUDA(cudaMemcpyAsync(t, v, (nloc + h->n_primal) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, nullptr, x, 1.0, t);
+  LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                          h->dual_l2.p, nullptr, x, 1.0, t));
   LAT_CHECK_LAUNCH();
   kinv(h, t, w);
-  k_axpby<<<ew_blocks(h, L), 256, 0, h->stream>>>(L, -1.0, x, 0.0, la_of(h, w));
+  LAT_LAUNCH(h, k_axpby<<<ew_blocks(h, L), 256, 0, h->stream>>>(L, -1.0, x, 0.0, la_of(h, w)));
   LAT_CHECK_LAUNCH();
 }
 
@@ -1044,31 +1132,31 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
   while (total < o->krylov_max_it) {
     // r = b - A x
     feti_operator(h, x, w, true);
-    k_axpby<<<eb, 256, 0, h->stream>>>(n, 1.0, b, -1.0, w);
+    LAT_LAUNCH(h, k_axpby<<<eb, 256, 0, h->stream>>>(n, 1.0, b, -1.0, w));
     dev_dot(h, n, w, w, sc);
     LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     rel = std::sqrt(hp[0]) / bnorm;
     if (rel <= o->krylov_rtol) break;
-    k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p);
-    k_gmres_init<<<1, 1, 0, h->stream>>>(m, h->gmres_small.p, sc);
+    LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p));
+    LAT_LAUNCH(h, k_gmres_init<<<1, 1, 0, h->stream>>>(m, h->gmres_small.p, sc));
     int j = 0;
     for (; j < m && total < o->krylov_max_it; ++j, ++total) {
       double* vj = h->V.p + (size_t)j * n;
       double* zj = h->Zk.p + (size_t)j * n;
-      run_block_precond(h, vj, zj, o->pcg_iters);
+      run_block_precond(h, vj, zj, o->pcg_iters, o->pcg_rtol);
       feti_operator(h, zj, w, true);
       // CGS with one re-orthogonalisation
       KernelTimer kt(h, "krylov_orth");
       for (int pass = 0; pass < 2; ++pass) {
-        k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, h->V.p, w, h->dots_part.p);
-        k_multidot_final<<<j + 1, 256, 0, h->stream>>>(nb, h->dots_part.p, pass == 0 ? hcol : h2);
-        k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j + 1, h->V.p, pass == 0 ? hcol : h2, -1.0, w);
+        LAT_LAUNCH(h, k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, h->V.p, w, h->dots_part.p));
+        LAT_LAUNCH(h, k_multidot_final<<<j + 1, 256, 0, h->stream>>>(nb, h->dots_part.p, pass == 0 ? hcol : h2));
+        LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j + 1, h->V.p, pass == 0 ? hcol : h2, -1.0, w));
       }
-      k_axpby<<<1, 256, 0, h->stream>>>(j + 1, 1.0, h2, 1.0, hcol);
+      LAT_LAUNCH(h, k_axpby<<<1, 256, 0, h->stream>>>(j + 1, 1.0, h2, 1.0, hcol));
       dev_dot(h, n, w, w, sc);
-      k_givens<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, hcol, sc, sc + 1);
-      k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p + (size_t)(j + 1) * n);
+      LAT_LAUNCH(h, k_givens<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, hcol, sc, sc + 1));
+      LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p + (size_t)(j + 1) * n));
       LAT_CHECK_LAUNCH();
       LAT_CUDA(cudaMemcpyAsync(hp, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -1080,8 +1168,8 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
       }
     }
     // x += Z y
-    k_gmres_solve<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, yv);
-    k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j, h->Zk.p, yv, 1.0, x);
+    LAT_LAUNCH(h, k_gmres_solve<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, yv));
+    LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j, h->Zk.p, yv, 1.0, x));
     LAT_CHECK_LAUNCH();
     if (rel <= o->krylov_rtol) break;
   }
@@ -1090,22 +1178,22 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
 }
 
 void run_feti_to_global(lat_ctx* h, const double* v, double* u) {
-  k_to_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
+  LAT_LAUNCH(h, k_to_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
       h->n_cells, h->n_P, h->copy_ptr.p, h->copy_idx.p, h->corner_of_node.p, h->pidx.p, h->dof_fixed.p,
-      v, pr_of(h, v), u);
+      v, pr_of(h, v), u));
   LAT_CHECK_LAUNCH();
 }
 
 void run_feti_from_global(lat_ctx* h, const double* u, double* v, bool split) {
   LAT_CUDA(cudaMemsetAsync(v, 0, h->n_krylov * sizeof(double), h->stream));
-  k_from_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
+  LAT_LAUNCH(h, k_from_global<<<div_up(h->n_glob_nodes, 256), 256, 0, h->stream>>>(h->n_glob_nodes, h->dim, h->n_nodes_cell,
       h->n_cells, h->n_P, h->copy_ptr.p, h->copy_idx.p, h->corner_of_node.p, h->pidx.p, h->dof_fixed.p,
-      u, split ? 1 : 0, v, pr_of(h, v));
+      u, split ? 1 : 0, v, pr_of(h, v)));
   LAT_CHECK_LAUNCH();
 }
 
 void run_axpy(lat_ctx* h, int64_t n, double a, const double* x, double* y) {
-  k_axpby<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, a, x, 1.0, y);
+  LAT_LAUNCH(h, k_axpby<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, a, x, 1.0, y));
   LAT_CHECK_LAUNCH();
 }
 
@@ -1124,6 +1212,8 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->krylov_max_it >= 1 && o->newton_max_it >= 1 && o->armijo_max_m >= 0 && o->pcg_iters >= 0,
               LAT_EINVAL, "iteration caps must be positive");
   LAT_REQUIRE(o->force_all || o->max_nr >= 1, LAT_EINVAL, "max_nr must be >= 1");
+  LAT_REQUIRE(o->pcg_rtol >= 0 && o->pcg_rtol < 1, LAT_EINVAL, "pcg_rtol in [0, 1)");
+  LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
 }
 
 // FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
@@ -1132,7 +1222,7 @@ void check_opts(const lat_newton_opts* o) {
 // cancel at interfaces and would make the relative Krylov tolerance an absolute floor).
 void newton_rhs(lat_ctx* h, const double* r_glob, double* b) {
   run_feti_from_global(h, r_glob, b, true);
-  k_axpby<<<ew_blocks(h, h->n_krylov), 256, 0, h->stream>>>(h->n_krylov, 0.0, b, -1.0, b);
+  LAT_LAUNCH(h, k_axpby<<<ew_blocks(h, h->n_krylov), 256, 0, h->stream>>>(h->n_krylov, 0.0, b, -1.0, b));
   LAT_CHECK_LAUNCH();
 }
 
@@ -1148,8 +1238,10 @@ extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
   o->krylov_rtol = h->prec == LAT_FP64 ? 1e-10 : 1e-6;
   o->krylov_max_it = 600;
   o->krylov_restart = 60;
-  o->pcg_iters = 5;
+  o->pcg_iters = 100;
   o->armijo_max_m = 30;
+  o->pcg_rtol = 1e-2;
+  o->interface_precond = 0;
   return LAT_OK;
 }
 
@@ -1167,6 +1259,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     ut.ensure(nd);
     double t0 = now_ms();
     bool neg = false;
+    h->pcg_its_total = 0;
     run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
     LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 at the initial guess");
     double rn = run_norm_free(h, h->r_glob.p);
@@ -1214,8 +1307,8 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       R.t_linesearch_ms += now_ms() - td;
       R.armijo_m_max = std::max(R.armijo_m_max, mm);
       if (h->verbose)
-        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d indef=%d krylov=%d (rel %.1e) m=%d%s\n",
-                     it, rn, rn / r0, h->n_r, h->n_keys, (int)h->indefinite, R.krylov_its_total, rel, mm,
+        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d indef=%d krylov=%d pcg=%lld (rel %.1e) m=%d%s\n",
+                     it, rn, rn / r0, h->n_r, h->n_keys, (int)h->indefinite, R.krylov_its_total, (long long)h->pcg_its_total, rel, mm,
                      accepted ? "" : " REJECTED");
       if (!accepted) {
         // leave u and the residual buffers consistent with u
@@ -1234,6 +1327,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     R.iterations = it;
     R.r_norm = rn;
+    R.pcg_its_total = (int32_t)h->pcg_its_total;
     R.converged = (rn <= o->newton_rtol * r0 || rn <= floor) ? 1 : 0;
     du.release();
     ut.release();
@@ -1277,7 +1371,7 @@ extern "C" lat_status feti_apply(lat_handle h, int32_t mode, const double* v, do
     LAT_REQUIRE(h->n_keys > 0, LAT_EINVAL, "call lattice_prepare_solver first");
     if (mode == 0) run_feti_operator(h, v, w);
     else if (mode == 1) run_kinv(h, v, w);
-    else if (mode == 2) run_block_precond(h, v, w, 5);
+    else if (mode == 2) run_block_precond(h, v, w, 5, 0.0);
     else throw LatError{LAT_EINVAL, "mode must be 0, 1 or 2"};
     LAT_CUDA(cudaStreamSynchronize(h->stream));
   });
@@ -1372,14 +1466,14 @@ __global__ void k_adj_w(int64_t n, const double* __restrict__ lam, const double*
 }  // namespace
 
 void run_f2d(lat_ctx* h, int64_t n, const float* x, double* y) {
-  k_f2d<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, x, y);
+  LAT_LAUNCH(h, k_f2d<<<ew_blocks(h, n), 256, 0, h->stream>>>(n, x, y));
   LAT_CHECK_LAUNCH();
 }
 void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed) {
-  k_mask<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, x, h->dof_fixed.p, keep_fixed, y);
+  LAT_LAUNCH(h, k_mask<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, x, h->dof_fixed.p, keep_fixed, y));
   LAT_CHECK_LAUNCH();
 }
 void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w) {
-  k_adj_w<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, lam, u, h->dof_fixed.p, w);
+  LAT_LAUNCH(h, k_adj_w<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, lam, u, h->dof_fixed.p, w));
   LAT_CHECK_LAUNCH();
 }

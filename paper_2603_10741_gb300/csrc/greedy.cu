@@ -187,20 +187,20 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
   h->g_scale.ensure(2);
   h->S.ensure(std::max(limit, h->n_cells));
   LAT_CUDA(cudaMemsetAsync(h->g_state.p, 0, 4 * sizeof(int), h->stream));
-  k_g_init<<<n_cols, kColThreads, 0, h->stream>>>(n_rows, T, h->g_delta.p, h->g_norms.p, h->g_inf.p,
-                                                  h->g_nrm2.p);
+  LAT_LAUNCH(h, k_g_init<<<n_cols, kColThreads, 0, h->stream>>>(n_rows, T, h->g_delta.p, h->g_norms.p, h->g_inf.p,
+                                                  h->g_nrm2.p));
   LAT_CHECK_LAUNCH();
   const int zgrid = std::min(div_up(n_rows, 256), 4 * h->n_sm);
   int* hp = reinterpret_cast<int*>(h->h_pinned);
   const int chunk = 8;
   for (int it0 = 0; it0 <= limit; it0 += chunk) {
     for (int it = it0; it < std::min(it0 + chunk, limit + 1); ++it) {
-      k_g_select<<<1, 1024, 0, h->stream>>>(it, n_cols, limit, eps, h->g_inf.p, h->g_nrm2.p,
-                                            h->g_state.p, h->S.p, h->g_maxres.p, h->g_scale.p);
-      k_g_zeta<<<zgrid, 256, 0, h->stream>>>(it, n_rows, h->g_delta.p, h->g_state.p, h->g_scale.p, h->g_Z.p);
+      LAT_LAUNCH(h, k_g_select<<<1, 1024, 0, h->stream>>>(it, n_cols, limit, eps, h->g_inf.p, h->g_nrm2.p,
+                                            h->g_state.p, h->S.p, h->g_maxres.p, h->g_scale.p));
+      LAT_LAUNCH(h, k_g_zeta<<<zgrid, 256, 0, h->stream>>>(it, n_rows, h->g_delta.p, h->g_state.p, h->g_scale.p, h->g_Z.p));
       KernelTimer kt(h, "greedy_update");
-      k_g_update<<<n_cols, kColThreads, 0, h->stream>>>(it, n_rows, n_cols, h->g_delta.p, h->g_Z.p,
-                                                        h->g_state.p, h->g_beta.p, h->g_inf.p, h->g_nrm2.p);
+      LAT_LAUNCH(h, k_g_update<<<n_cols, kColThreads, 0, h->stream>>>(it, n_rows, n_cols, h->g_delta.p, h->g_Z.p,
+                                                        h->g_state.p, h->g_beta.p, h->g_inf.p, h->g_nrm2.p));
     }
     LAT_CHECK_LAUNCH();
     LAT_CUDA(cudaMemcpyAsync(hp, h->g_state.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -218,8 +218,8 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
     a32 = h->alpha32.p;
   }
   if (n_r > 0) {
-    k_g_alpha<float><<<div_up(n_cols, 128), 128, 0, h->stream>>>(n_r, n_cols, h->S.p, h->g_beta.p,
-                                                                 h->g_norms.p, h->alpha.p, a32);
+    LAT_LAUNCH(h, k_g_alpha<float><<<div_up(n_cols, 128), 128, 0, h->stream>>>(n_r, n_cols, h->S.p, h->g_beta.p,
+                                                                 h->g_norms.p, h->alpha.p, a32));
     LAT_CHECK_LAUNCH();
   }
   if (S_out) LAT_CUDA(cudaMemcpyAsync(S_out, h->S.p, n_r * sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
@@ -256,7 +256,7 @@ void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool
   if (force_all) {
     h->n_r = h->n_cells;
     h->S.ensure(h->n_cells);
-    k_iota<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->S.p);
+    LAT_LAUNCH(h, k_iota<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->S.p));
     LAT_CHECK_LAUNCH();
   } else {
     h->T.ensure((size_t)h->n_cells * h->nnz);
@@ -272,7 +272,7 @@ void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool
   if (h->prec != LAT_FP64) {
     const int64_t n = (int64_t)h->n_r * h->nnz;
     h->Kp32.ensure(n);
-    k_to_f32<<<div_up(n, 256), 256, 0, h->stream>>>(n, h->Kp.p, h->Kp32.p);
+    LAT_LAUNCH(h, k_to_f32<<<div_up(n, 256), 256, 0, h->stream>>>(n, h->Kp.p, h->Kp32.p));
     LAT_CHECK_LAUNCH();
   }
 }

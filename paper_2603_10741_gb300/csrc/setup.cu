@@ -192,18 +192,33 @@ void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
   }
   LAT_REQUIRE(nc == (1 << d), LAT_EINVAL, "reference cell must have a node at every cube corner");
   h->corner_of_node.upload(corner, h->stream);
+  // remaining dofs ordered interior first, then the non-corner dofs on the cell boundary (the
+  // dual dofs): the Gauss-Jordan sweep over the interior block then leaves the dual Schur
+  // complement in the trailing block (Dirichlet interface preconditioner)
   std::vector<int> rdofs, pdofs(nc * d), rpos(nl, -1);
-  for (int a = 0; a < nn; ++a)
-    for (int i = 0; i < d; ++i) {
-      if (corner[a] >= 0) {
-        pdofs[corner[a] * d + i] = a * d + i;
-      } else {
+  auto on_boundary = [&](int a) {
+    for (int k = 0; k < d; ++k) {
+      double x = ds->X_ref[(size_t)a * d + k];
+      if (std::fabs(x) < 1e-12 || std::fabs(x - 1.0) < 1e-12) return true;
+    }
+    return false;
+  };
+  for (int pass = 0; pass < 2; ++pass)
+    for (int a = 0; a < nn; ++a) {
+      if (corner[a] >= 0 || on_boundary(a) != (pass == 1)) continue;
+      for (int i = 0; i < d; ++i) {
         rpos[a * d + i] = (int)rdofs.size();
         rdofs.push_back(a * d + i);
       }
     }
+  for (int a = 0; a < nn; ++a)
+    if (corner[a] >= 0)
+      for (int i = 0; i < d; ++i) pdofs[corner[a] * d + i] = a * d + i;
   h->n_P = nc * d;
   h->n_R = (int)rdofs.size();
+  h->n_I = 0;
+  for (int a = 0; a < nn; ++a)
+    if (corner[a] < 0 && !on_boundary(a)) h->n_I += d;
   h->rdofs.upload(rdofs, h->stream);
   h->pdofs.upload(pdofs, h->stream);
   h->rpos.upload(rpos, h->stream);
@@ -425,7 +440,7 @@ extern "C" lat_status lattice_setup(const lat_mesh_desc* ds, lat_precision prec,
     DBuf<double> th;
     th.upload(h->h_mu_scale, h->stream);
     h->mu_cell.ensure(h->n_cells);
-    k_set_mu<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->mu, th.p, h->mu_cell.p);
+    LAT_LAUNCH(h, k_set_mu<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->mu, th.p, h->mu_cell.p));
     LAT_CHECK_LAUNCH();
     LAT_CUDA(cudaMallocHost(&h->h_pinned, 64 * sizeof(double)));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
@@ -501,7 +516,7 @@ extern "C" lat_status lattice_set_mu_scale(lat_handle h, const double* th) {
     h->h_mu_scale.assign(th, th + h->n_cells);
     DBuf<double> t;
     t.upload(h->h_mu_scale, h->stream);
-    k_set_mu<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->mu, t.p, h->mu_cell.p);
+    LAT_LAUNCH(h, k_set_mu<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->mu, t.p, h->mu_cell.p));
     LAT_CHECK_LAUNCH();
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     t.release();
@@ -512,8 +527,8 @@ extern "C" lat_status lattice_predictor(lat_handle h, double load, const double*
                                         const double* up2, double* out) {
   if (!h || !out) return LAT_EINVAL;
   return guard(h, [&] {
-    k_predictor<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, load, up, up2, h->aff_unit.p,
-                                                             h->dir_unit.p, h->dof_fixed.p, out);
+    LAT_LAUNCH(h, k_predictor<<<div_up(h->n_dof, 256), 256, 0, h->stream>>>(h->n_dof, load, up, up2, h->aff_unit.p,
+                                                             h->dir_unit.p, h->dof_fixed.p, out));
     LAT_CHECK_LAUNCH();
   });
 }
@@ -522,8 +537,8 @@ extern "C" lat_status lattice_gather(lat_handle h, const double* u, double* x) {
   if (!h || !u || !x) return LAT_EINVAL;
   return guard(h, [&] {
     dim3 grid(div_up(h->n_cells, 128), h->n_loc);
-    k_gather<<<grid, 128, 0, h->stream>>>(h->n_cells, h->n_loc, h->dim, h->n_nodes_cell,
-                                          h->cell_nodes.p, u, x);
+    LAT_LAUNCH(h, k_gather<<<grid, 128, 0, h->stream>>>(h->n_cells, h->n_loc, h->dim, h->n_nodes_cell,
+                                          h->cell_nodes.p, u, x));
     LAT_CHECK_LAUNCH();
   });
 }
@@ -612,4 +627,10 @@ extern "C" lat_status lattice_kernel_time(lat_handle h, const char* name, double
     *total_ms = t;
     *launches = n;
   });
+}
+
+extern "C" lat_status lattice_launch_count(lat_handle h, int64_t* launches) {
+  if (!h || !launches) return LAT_EINVAL;
+  *launches = h->n_launch;
+  return LAT_OK;
 }

@@ -23,7 +23,7 @@ EXPORTS = ["lattice_setup", "lattice_destroy", "lattice_sizes", "lattice_last_er
            "greedy_select", "select_principal_cells", "apply_reduced_tangent", "lattice_default_opts",
            "newton_step", "adjoint_gradient", "feti_apply", "lattice_prepare_solver", "feti_to_global",
            "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve",
-           "lattice_set_timing", "lattice_kernel_time"]
+           "lattice_set_timing", "lattice_kernel_time", "lattice_launch_count"]
 
 
 class LatticeError(RuntimeError):
@@ -51,14 +51,15 @@ class NewtonOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_nr", C.c_int32), ("force_all", C.c_int32),
                 ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("krylov_rtol", C.c_double),
                 ("krylov_max_it", C.c_int32), ("krylov_restart", C.c_int32), ("pcg_iters", C.c_int32),
-                ("armijo_max_m", C.c_int32)]
+                ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32)]
 
 
 class NewtonReport(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("converged", C.c_int32), ("r0_norm", C.c_double),
                 ("r_norm", C.c_double), ("n_r_last", C.c_int32), ("krylov_its_total", C.c_int32),
                 ("armijo_m_max", C.c_int32), ("t_residual_ms", C.c_double), ("t_select_ms", C.c_double),
-                ("t_setup_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_linesearch_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_linesearch_ms", C.c_double),
+                ("pcg_its_total", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -92,6 +93,7 @@ def load_library(path: str = LIB_PATH):
         "lattice_checkpoint_load": [P, C.c_char_p, P, P, P, P],
         "lattice_set_timing": [P, I32],
         "lattice_kernel_time": [P, C.c_char_p, P, P],
+        "lattice_launch_count": [P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -324,6 +326,11 @@ class Lattice:
         t, n = C.c_double(0), C.c_int32(0)
         self._check(self._lib.lattice_kernel_time(self.h, name.encode(), C.byref(t), C.byref(n)))
         return t.value, n.value
+
+    def lattice_launch_count(self):
+        n = C.c_int64(0)
+        self._check(self._lib.lattice_launch_count(self.h, C.byref(n)))
+        return n.value
 
     def lattice_checkpoint_save(self, path, step, load, u, u_prev=None):
         self._check(self._lib.lattice_checkpoint_save(self.h, str(path).encode(), int(step), float(load),
