@@ -129,6 +129,22 @@ lat_status greedy_select(lat_handle h, const double* T, int64_t n_rows, int32_t 
                          int32_t max_nr, int32_t* S, int32_t* n_r, double* alpha, double* beta,
                          double* Z, double* max_res);
 
+/* Allocation-free Algorithm 1 for callers that cannot allocate device memory (a memory arena
+ * that owns the device budget, a host application that forbids cudaMalloc/cudaFree, code that
+ * cannot create a handle since lattice_setup allocates).  The paper has no counterpart: this
+ * is a library variant of greedy_select.  Same arguments and results as greedy_select for
+ * T, n_rows, n_cols, eps, max_nr, S, n_r, alpha, with no handle: the work runs on cuda_stream
+ * (NULL = legacy default stream).  All workspace lives in one file-scope device array of
+ * 16 MiB (2 Mi doubles) that every device loading the library holds until process exit; it
+ * must fit Delta (n_cols * n_rows), Z (min(max_nr, n_cols, n_rows) * n_rows), beta and a few
+ * per-column vectors, else LAT_EINVAL is returned before any work.  No cudaMalloc, cudaFree or
+ * allocating library call is made.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress with that device current), so make that first call before any
+ * stream capture.  Every call reuses the same array (its state is reset at the start of each
+ * call); calls that overlap on the GPU, from any stream or thread, race and must be avoided. */
+lat_status greedy_select_static(const double* T, int64_t n_rows, int32_t n_cols, double eps, int32_t max_nr,
+                                int32_t* S, int32_t* n_r, double* alpha, void* cuda_stream);
+
 /* Principal cells for state u_glob (dev): snapshots with the reduced rule for all cells,
  * Algorithm 1 with tolerance eps, coefficients alpha (Section 3.2.2), then the principal
  * tangents K^r = K^{s_r}(u^{s_r}) with the full rule (Eq. reducedbasis).  force_all != 0 skips

@@ -295,3 +295,100 @@ extern "C" lat_status select_principal_cells(lat_handle h, const double* u_glob,
     if (n_r) *n_r = h->n_r;
   });
 }
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of greedy_select.
+//
+// Some callers cannot allocate device memory: code running inside a memory pool or arena that
+// owns the whole device budget, plugins whose host application forbids cudaMalloc/cudaFree on
+// its hot path (they synchronise the device and can stall other streams), and code that must
+// not create a lattice handle (lattice_setup allocates).  This entry point runs the same
+// Algorithm 1 kernels as greedy_select on the caller's snapshot matrix, with every workspace
+// carved out of one file-scope device array of fixed size.  The array lives on every device
+// that loads the library, from load until process exit.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticGreedyDoubles = size_t(2) << 20;   // 2 Mi doubles = 16 MiB
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) double g_static_greedy[kStaticGreedyDoubles];
+
+// device address of g_static_greedy per device, looked up once with that device current
+double* g_static_ptr[kStaticMaxDevices] = {nullptr};
+
+struct StaticLayout {
+  double *delta, *Z, *beta, *norms, *inf, *nrm2, *maxres, *scale;
+  int* state;
+  int* S;
+  size_t doubles;
+};
+
+StaticLayout static_layout(double* base, int64_t n_rows, int n_cols, int limit) {
+  StaticLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    double* p = base ? base + off : nullptr;
+    off += (n + 31) & ~size_t(31);   // keep every piece 256-byte aligned
+    return p;
+  };
+  L.delta = take((size_t)n_cols * n_rows);
+  L.Z = take((size_t)limit * n_rows);
+  L.beta = take((size_t)limit * n_cols);
+  L.norms = take(n_cols);
+  L.inf = take(n_cols);
+  L.nrm2 = take(n_cols);
+  L.maxres = take(limit + 1);
+  L.scale = take(2);
+  L.state = reinterpret_cast<int*>(take(2));          // 4 ints
+  L.S = reinterpret_cast<int*>(take((limit + 1) / 2 + 1));
+  L.doubles = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" lat_status greedy_select_static(const double* T, int64_t n_rows, int32_t n_cols, double eps,
+                                           int32_t max_nr, int32_t* S, int32_t* n_r, double* alpha,
+                                           void* cuda_stream) {
+  if (!T || !S || !n_r || n_rows <= 0 || n_cols <= 0 || max_nr < 1) return LAT_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int limit = (int)std::min<int64_t>({(int64_t)max_nr, (int64_t)n_cols, n_rows});
+  if (static_layout(nullptr, n_rows, n_cols, limit).doubles > kStaticGreedyDoubles) return LAT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return LAT_ECUDA;
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_greedy) != cudaSuccess || !p) return LAT_ECUDA;
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  const StaticLayout W = static_layout(g_static_ptr[dev], n_rows, n_cols, limit);
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return LAT_ECUDA;
+  if (cudaMemsetAsync(W.state, 0, 4 * sizeof(int), st) != cudaSuccess) return LAT_ECUDA;
+  k_g_init<<<n_cols, kColThreads, 0, st>>>(n_rows, T, W.delta, W.norms, W.inf, W.nrm2);
+  const int zgrid = std::min(div_up(n_rows, 256), 4 * n_sm);
+  int hstate[2] = {0, 0};
+  const int chunk = 8;
+  for (int it0 = 0; it0 <= limit; it0 += chunk) {
+    for (int it = it0; it < std::min(it0 + chunk, limit + 1); ++it) {
+      k_g_select<<<1, 1024, 0, st>>>(it, n_cols, limit, eps, W.inf, W.nrm2, W.state, W.S, W.maxres, W.scale);
+      k_g_zeta<<<zgrid, 256, 0, st>>>(it, n_rows, W.delta, W.state, W.scale, W.Z);
+      k_g_update<<<n_cols, kColThreads, 0, st>>>(it, n_rows, n_cols, W.delta, W.Z, W.state, W.beta, W.inf, W.nrm2);
+    }
+    if (cudaGetLastError() != cudaSuccess) return LAT_ECUDA;
+    if (cudaMemcpyAsync(hstate, W.state, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return LAT_ECUDA;
+    if (hstate[0]) break;
+  }
+  if (!hstate[0]) return LAT_EINVAL;
+  const int k = hstate[1];
+  if (k > 0 && alpha)
+    k_g_alpha<float><<<div_up(n_cols, 128), 128, 0, st>>>(k, n_cols, W.S, W.beta, W.norms, alpha, nullptr);
+  if (cudaGetLastError() != cudaSuccess) return LAT_ECUDA;
+  if (k > 0 && cudaMemcpyAsync(S, W.S, k * sizeof(int), cudaMemcpyDeviceToDevice, st) != cudaSuccess) return LAT_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return LAT_ECUDA;
+  *n_r = k;
+  return LAT_OK;
+}

@@ -23,7 +23,7 @@ EXPORTS = ["lattice_setup", "lattice_destroy", "lattice_sizes", "lattice_last_er
            "greedy_select", "select_principal_cells", "apply_reduced_tangent", "lattice_default_opts",
            "newton_step", "adjoint_gradient", "feti_apply", "lattice_prepare_solver", "feti_to_global",
            "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve",
-           "lattice_set_timing", "lattice_kernel_time", "lattice_launch_count"]
+           "lattice_set_timing", "lattice_kernel_time", "lattice_launch_count", "greedy_select_static"]
 
 
 class LatticeError(RuntimeError):
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
         "lattice_set_timing": [P, I32],
         "lattice_kernel_time": [P, C.c_char_p, P, P],
         "lattice_launch_count": [P, P],
+        "greedy_select_static": [P, I64, I32, D, I32, P, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -145,6 +146,27 @@ def case_arrays(case):
                 dof_fixed=fixed, dirichlet_unit=dunit, affine_unit=aff,
                 mu_scale=np.ascontiguousarray(case.mu_scale, dtype=np.float64),
                 mu=float(case.mu), lam=float(case.lam), n_glob_nodes=lat.n_nodes)
+
+
+def greedy_select_static(T, eps, max_nr, stream=None):
+    """Algorithm 1 without any device allocation by the library (greedy_select_static).
+
+    For callers that cannot allocate device memory; the workspace is the library's fixed 16 MiB
+    device array, shared by every call (calls must not overlap on the GPU).  T is a device
+    tensor [n_cols, n_rows] (column s contiguous); S and alpha are allocated here by torch, the
+    caller's allocator, and passed in.  Returns (S [n_r] int32, alpha [n_r, n_cols]).
+    """
+    n_cols, n_rows = T.shape
+    stream = torch.cuda.current_stream() if stream is None else stream
+    S = torch.zeros(max_nr, dtype=torch.int32, device=T.device)
+    alpha = torch.zeros((max_nr, n_cols), dtype=torch.float64, device=T.device)
+    n_r = C.c_int32(0)
+    st = lib().greedy_select_static(_ptr(T), n_rows, n_cols, float(eps), int(max_nr), _ptr(S), C.byref(n_r),
+                                    _ptr(alpha), C.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise LatticeError(st, "greedy_select_static failed (sizes beyond the 16 MiB workspace give LAT_EINVAL)")
+    k = n_r.value
+    return S[:k], alpha[:k]
 
 
 class Lattice:
