@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--case", default="ring32")
-    p.add_argument("--state-step", type=int, default=10)
+    p.add_argument("--state-step", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the full-path and mixed comparisons")
     return p.parse_args()
@@ -209,7 +209,7 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------------------------
 KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
-           "local_segmm", "local_gemv", "gj_update", "krylov_orth"]
+           "local_segmm", "local_gemv", "local_tc", "gj_update", "krylov_orth"]
 
 
 def kernel_work(name, s, n_r, n_keys, prec_bytes):
@@ -223,7 +223,7 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes):
     """
     n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
     rows = s.n_r_local + s.n_p_local
-    if name in ("local_segmm", "local_gemv"):
+    if name in ("local_segmm", "local_gemv", "local_tc"):
         return 2.0 * rows * s.n_r_local * n_s, "flops"
     if name == "apply_reduced":
         return 2.0 * n_r * nnz * n_s, "flops"
@@ -239,7 +239,7 @@ def run_ours(args):
     import __graft_entry__ as g
     g.build()
     import latgen
-    from paper_2603_10741_gb300 import LAT_FP64, LAT_MIXED_FP32, Lattice, solve_load_path
+    from paper_2603_10741_gb300 import LAT_FP64, LAT_MIXED_BF16, LAT_MIXED_FP32, Lattice, solve_load_path
 
     ws, rank, local = dist_init(args)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -355,6 +355,22 @@ def run_ours(args):
                              "phase_ms": {k: reps_mix[-1][k] for k in ("t_residual_ms", "t_select_ms",
                                                                        "t_setup_ms", "t_krylov_ms")},
                              "kernels": kt_mix}
+        # BF16 principal blocks on the tensor cores (tcgen05), FP32 accumulation
+        lat_b = Lattice.from_case(case, LAT_MIXED_BF16)
+        opts_b = lat_b.lattice_default_opts()
+        ms_bf, reps_bf, kt_bf, _ = time_newton(lat_b, opts_b, args.steps, 1, None, timing=True)
+        out["mixed_bf16"] = {"ms_per_step": ms_bf, "value": ws * n_dof / (ms_bf * 1e-3) / 1e9,
+                             "krylov_its": reps_bf[-1]["krylov_its_total"], "n_r": reps_bf[-1]["n_r_last"],
+                             "phase_ms": {k: reps_bf[-1][k] for k in ("t_residual_ms", "t_select_ms",
+                                                                      "t_setup_ms", "t_krylov_ms")},
+                             "kernels": kt_bf}
+        if "local_tc" in kt_bf:
+            work, _ = kernel_work("local_tc", s, None, None, 2)
+            ach = work / (kt_bf["local_tc"]["avg_us"] * 1e-6) / 1e12
+            out["mixed_bf16"]["tensor_roofline"] = {"kernel": "local_tc", "bound": "tensor", "achieved": ach,
+                                                    "peak": bf16_peak, "unit": "TFLOP/s",
+                                                    "frac": ach / bf16_peak, "peak_source": peak_src}
+        lat_b.close()
     # reduced tangent action alone (selection of the benchmark state), L2 flushed between calls
     out["apply"] = bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src)
     # end to end through host buffers: H2D of the state, one Newton iteration, D2H of the result

@@ -124,16 +124,132 @@ __global__ void __launch_bounds__(256)
   store_ya<T, D, FETI>(A, Y, s, a, y);
 }
 
+// Shared-memory staged form.  A CTA is 8 warps; warp w owns local node a = 8 blockIdx.y + w and
+// its lanes own CPT x 32 consecutive cells.  Each warp stages its node's principal blocks
+// K^r_{a,:} for a chunk of RCH principals into its own slice of shared memory (so only
+// __syncwarp is needed), keeps the neighbour values x_b of its cells in registers, and for every
+// principal forms z = K^r_{a,:} x (broadcast shared loads, CPT cells per load) before the
+// alpha-weighted accumulation y += alpha_r^s z: the alpha combination is the epilogue of each
+// principal's SpMV.
+template <int D>
+struct StageCfg {
+  static constexpr int MAXNB = D == 2 ? 9 : 27;  // node blocks per row of a Q1 pattern
+  static constexpr int CPT = D == 2 ? 2 : 1;     // cells per thread
+};
+
+template <typename T, int D>
+__host__ __device__ constexpr int stage_rch() {
+  return D == 2 ? (sizeof(T) == 4 ? 32 : 16) : (sizeof(T) == 4 ? 8 : 4);
+}
+
+template <typename T, int D, bool FETI>
+__global__ void __launch_bounds__(256)
+    k_apply_staged(ApplyArgs A, int n_r, const T* __restrict__ Kp, const T* __restrict__ alpha,
+                   const T* __restrict__ X, T* __restrict__ Y) {
+  constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
+  constexpr int DD = D * D;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.y * 8 + warp;
+  if (a >= A.nn) return;                         // whole warp leaves together
+  T* ks = reinterpret_cast<T*>(sm_raw) + (size_t)warp * MAXNB * RCH * DD;
+  const int b0 = A.blk_ptr[a];
+  const int nb = A.blk_ptr[a + 1] - b0;
+  int cell[CPT];
+  bool live[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int c = blockIdx.x * 32 * CPT + k * 32 + lane;
+    live[k] = c < A.n_cells;
+    cell[k] = live[k] ? c : A.n_cells - 1;
+  }
+  T xb[MAXNB][D][CPT];
+#pragma unroll
+  for (int bi = 0; bi < MAXNB; ++bi) {
+    if (bi < nb) {
+      const int b = A.blk_col[b0 + bi];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) {
+        T v[D];
+        load_xb<T, D, FETI>(A, X, cell[k], b, v);
+#pragma unroll
+        for (int j = 0; j < D; ++j) xb[bi][j][k] = v[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) xb[bi][j][k] = T(0);
+    }
+  }
+  T y[D][CPT];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) y[i][k] = T(0);
+  for (int r0 = 0; r0 < n_r; r0 += RCH) {
+    const int nr = min(RCH, n_r - r0);
+    __syncwarp();
+    for (int t = lane; t < nb * nr * DD; t += 32) {
+      const int bi = t / (nr * DD), rem = t - bi * nr * DD;
+      const int r = rem / DD, e = rem - r * DD;
+      ks[(bi * RCH + r) * DD + e] = Kp[(size_t)(r0 + r) * A.nnz + (size_t)(b0 + bi) * DD + e];
+    }
+    __syncwarp();
+    for (int r = 0; r < nr; ++r) {
+      T al[CPT];
+#pragma unroll
+      for (int k = 0; k < CPT; ++k) al[k] = alpha[(size_t)(r0 + r) * A.n_cells + cell[k]];
+      T z[D][CPT];
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) z[i][k] = T(0);
+#pragma unroll
+      for (int bi = 0; bi < MAXNB; ++bi) {
+        if (bi < nb) {
+          const T* kb = ks + (bi * RCH + r) * DD;
+          T kv[DD];
+#pragma unroll
+          for (int e = 0; e < DD; ++e) kv[e] = kb[e];
+#pragma unroll
+          for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j)
+#pragma unroll
+              for (int k = 0; k < CPT; ++k) z[i][k] = fma(kv[i * D + j], xb[bi][j][k], z[i][k]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) y[i][k] = fma(al[k], z[i][k], y[i][k]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    if (!live[k]) continue;
+    T v[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) v[i] = y[i][k];
+    store_ya<T, D, FETI>(A, Y, cell[k], a, v);
+  }
+}
+
 template <typename T, int D, bool FETI>
 void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T* X, T* Y) {
-  dim3 blk(32, 8);
-  dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
   if (h->force_all) {
+    dim3 blk(32, 8);
+    dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
   } else {
+    constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
+    const size_t shm = (size_t)8 * MAXNB * RCH * D * D * sizeof(T);
+    LAT_CUDA(cudaFuncSetAttribute(k_apply_staged<T, D, FETI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    dim3 grid(div_up(h->n_cells, 32 * CPT), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_reduced");
-    LAT_LAUNCH(h, k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
+    LAT_LAUNCH(h, k_apply_staged<T, D, FETI><<<grid, 256, shm, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
   }
   LAT_CHECK_LAUNCH();
 }

@@ -332,3 +332,5 @@ void run_f2d(lat_ctx* h, int64_t n, const float* x, double* y);
 void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed);
 void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w);
 void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool force_all);
+void run_g_to_bf16(lat_ctx* h, size_t n);
+void run_local_tc(lat_ctx* h, const double* X, double* Y);

@@ -875,6 +875,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   crep.release();
   LAT_REQUIRE(!(fl & 1), LAT_EINDEFINITE, "a local remaining-DOF matrix or the coarse matrix is singular");
   h->indefinite = (fl & 2) != 0;
+  if (h->prec == LAT_MIXED_BF16) run_g_to_bf16(h, gsz);
   if (h->prec != LAT_FP64) {
     h->G32.ensure(gsz);
     LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, gsz), 256, 0, h->stream>>>(gsz, h->G.p, h->G32.p));
@@ -941,6 +942,8 @@ void kinv(lat_ctx* h, const double* v, double* w) {
       LAT_LAUNCH(h, k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nR, nP, h->G.p, h->key_slot.p, h->c_cell.p,
                                                         h->rdofs.p, h->pdofs.p, v, wl));
     }
+  } else if (h->prec == LAT_MIXED_BF16) {
+    run_local_tc(h, v, wl);   // tcgen05, BF16 operands, FP32 accumulation
   } else {
     KernelTimer kt(h, "local_segmm");
     dim3 grid(h->max_tiles, div_up(nR + nP, 64));
@@ -1174,6 +1177,12 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
     if (rel <= o->krylov_rtol) break;
   }
   if (rel_out) *rel_out = rel;
+  if (h->prec == LAT_MIXED_BF16) {
+    int fl = 0;
+    LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    LAT_REQUIRE(!(fl & 4), LAT_ETIMEOUT, "a tensor-core wait in the local product gave up");
+  }
   return total;
 }
 

@@ -120,6 +120,10 @@ void build_pattern_and_colors(lat_ctx* h, const int* E) {
     for (int b : nbr[a]) h->h_blk_col.push_back(b);
   }
   h->n_blk = h->h_blk_ptr[nn];
+  // the staged apply keeps one row of node blocks per warp: at most 3^d blocks (Q1 stencil)
+  for (int a = 0; a < nn; ++a)
+    LAT_REQUIRE(h->h_blk_ptr[a + 1] - h->h_blk_ptr[a] <= (h->dim == 2 ? 9 : 27), LAT_EINVAL,
+                "a node couples to more than 3^d nodes: not a Q1 mesh");
   h->nnz = (int64_t)h->n_blk * h->dim * h->dim;
   std::vector<int> eb((size_t)h->n_el * nen * nen);
   for (int e = 0; e < h->n_el; ++e)
@@ -474,7 +478,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
   rel(h->key_of_cell); rel(h->key_slot); rel(h->perm); rel(h->seg_ptr); rel(h->tile_seg);
   rel(h->tile_c0); rel(h->key_list); rel(h->solver_int); rel(h->delta_cell); rel(h->c_cell);
-  rel(h->G); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->G16); rel(h->KRP); rel(h->Coarse);
+  rel(h->G); rel(h->G16); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->G16); rel(h->KRP); rel(h->Coarse);
   rel(h->CoarseInv); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);

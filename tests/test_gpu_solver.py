@@ -188,3 +188,39 @@ def test_checkpoint_roundtrip(L, tmp_path):
     assert step == 3 and load == -0.25
     assert torch.equal(a, a2) and torch.equal(b, b2)
     lat.close()
+
+
+@pytest.mark.parametrize("name", ["ring8"])
+def test_bf16_tensor_core_local_product(L, name):
+    """BF16 mode: the tcgen05 principal-block product inside K^-rom agrees with the FP64 one to
+    BF16 accuracy (8-bit mantissa operands, FP32 accumulation over ~570 terms)."""
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    ud = torch.tensor(_u0(prob, 1, 0.0005, 4), device="cuda")
+    outs = []
+    for prec in (0, 2):
+        lat = L.Lattice.from_case(case, prec)
+        opts = lat.lattice_default_opts(eps=1e-3)
+        lat.select_principal_cells(ud, 1e-3, 256)
+        lat.lattice_prepare_solver(ud, opts)
+        s = lat.sizes
+        rng = np.random.default_rng(5)
+        v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
+        outs.append(lat.feti_apply(1, v)[: s.n_loc * s.n_cells + s.n_primal].cpu().numpy())
+        lat.close()
+    ref, got = outs
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 2e-2, err
+
+
+def test_newton_bf16_mode_ring4(L):
+    """BF16 preconditioner blocks, FP64 residual/operator/update: same solution as the oracle."""
+    from paper_2603_10741_gb300 import solve_load_path
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, _ = ON.load_path(prob, n_steps=2, tol=1e-12)
+    lat = L.Lattice.from_case(case, 2)
+    u, reps = solve_load_path(lat, case, lat.lattice_default_opts(newton_rtol=1e-10), steps=2)
+    err = np.linalg.norm(u.cpu().numpy() - ref[-1]) / np.linalg.norm(ref[-1])
+    assert err < 1e-8, err
+    lat.close()
