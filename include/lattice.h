@@ -69,6 +69,9 @@ typedef struct {
   const double* affine_unit;   /* [n_glob_nodes*dim] first-step predictor per unit load parameter */
   const double* mu_scale;      /* [n_cells] shear-modulus factor theta_s, or NULL for all ones */
   double mu, lam;              /* Lame parameters */
+  const int32_t* cell_layer;   /* [n_cells] index of the cell's layer along the load axis, or NULL;
+                                  with it the coarse problem is solved through its
+                                  block-tridiagonal structure instead of a dense inverse */
 } lat_mesh_desc;
 
 typedef struct {
@@ -92,6 +95,9 @@ typedef struct {
 lat_status lattice_setup(const lat_mesh_desc* desc, lat_precision precision, void* cuda_stream,
                          lat_handle* out);
 lat_status lattice_destroy(lat_handle h);
+/* The FETI-DP sizes (n_r_local, n_p_local, n_primal, n_lambda, n_krylov) change when
+ * newton_step, lattice_prepare_solver or adjoint_gradient enrich the primal set
+ * (Section 3.3.2): query them again before sizing saddle-point buffers. */
 lat_status lattice_sizes(lat_handle h, lat_sizes* out);
 const char* lattice_last_error(lat_handle h);
 /* Replace the per-cell shear-modulus factors theta_s (host [n_cells]). */
@@ -175,6 +181,10 @@ typedef struct {
                               (0: always pcg_iters iterations) */
   int32_t interface_precond; /* M of the interface PCG: 0 Dirichlet B_D S_DD B_D^T with the local
                                 dual Schur complements of the principals, 1 lumped B_D K_DD B_D^T */
+  int32_t max_enrich;      /* cap on the primal enrichment level (Section 3.3.2): when a
+                              principal's remaining block is not positive definite, primal
+                              nodes are added on every cell edge (level L: the nodes nearest to
+                              the points j/2^L of each edge) for all cells, and kept */
 } lat_newton_opts;
 
 typedef struct {
@@ -187,11 +197,12 @@ typedef struct {
   int32_t armijo_m_max;
   double t_residual_ms, t_select_ms, t_setup_ms, t_krylov_ms, t_linesearch_ms; /* phase times */
   int32_t pcg_its_total;   /* interface PCG iterations inside the preconditioner */
+  int32_t enrich_level;    /* primal enrichment level in use at exit */
 } lat_newton_report;
 
 /* Default options (eps 3e-4 in 2D and 5e-3 in 3D, max_nr 256, newton_rtol 1e-8, krylov_rtol
  * 1e-10 for FP64 and 1e-6 for the mixed modes, restart 60, interface PCG to 1e-2 with at most 100
- * iterations, Armijo cap 30). */
+ * iterations, Armijo cap 30, Dirichlet interface preconditioner, enrichment up to level 3). */
 lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 
 /* Newton-Raphson for one load step (Section 2.2.5) from the initial guess in u_glob (dev,

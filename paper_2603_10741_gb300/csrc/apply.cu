@@ -9,15 +9,16 @@
 // combination is fused: per node block (a, b) the thread forms sum_r alpha_r^s K^r_ab in
 // registers and multiplies by x_b once.
 //
-// FETI mode (Section 3.3.1): the input is the remaining part of a saddle-point vector, the corner
-// values come from the global primal vector through the cell's primal map; outputs at fixed
-// local DOFs are zeroed, outputs at corner rows are kept for the primal assembly.
+// FETI mode (Section 3.3.1): the input is the remaining part of a saddle-point vector, the primal
+// values (corners, and edge nodes after enrichment) come from the global primal vector through
+// the cell's primal map; outputs at fixed local DOFs are zeroed, outputs at primal rows are kept
+// for the primal assembly.
 #include "common.cuh"
 
 namespace {
 
 struct ApplyArgs {
-  int n_cells, nn;
+  int n_cells, nn, n_P;
   int64_t nnz;
   const int* blk_ptr;
   const int* blk_col;
@@ -35,7 +36,7 @@ __device__ __forceinline__ void load_xb(const ApplyArgs& A, const T* __restrict_
     if (c >= 0) {
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        const int p = A.pidx[(size_t)s * (D << D) + c * D + j];
+        const int p = A.pidx[(size_t)s * A.n_P + c * D + j];
         xb[j] = p >= 0 ? (T)A.xP[p] : T(0);
       }
       return;
@@ -269,7 +270,7 @@ void dispatch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const
 
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti) {
   LAT_REQUIRE(h->n_r > 0 && h->Kp.p, LAT_EINVAL, "no principal cells selected");
-  ApplyArgs A{h->n_cells, h->n_nodes_cell, h->nnz, h->blk_ptr.p, h->blk_col.p,
+  ApplyArgs A{h->n_cells, h->n_nodes_cell, h->n_P, h->nnz, h->blk_ptr.p, h->blk_col.p,
               h->corner_of_node.p, h->pidx.p, h->loc_fixed.p, xP};
   if (dtype == 0) {
     dispatch<double>(h, A, h->Kp.p, h->alpha.p, (const double*)x, (double*)y, feti);

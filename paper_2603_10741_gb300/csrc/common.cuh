@@ -103,6 +103,9 @@ struct lat_ctx {
   DBuf<uint8_t> dof_fixed;            // [n_dof]
   DBuf<double> dir_unit, aff_unit;    // [n_dof]
   std::vector<uint8_t> h_dof_fixed;
+  std::vector<double> h_X_ref;          // host copies kept to rebuild the FETI-DP index sets
+  std::vector<int> h_cell_nodes, h_cptr, h_cidx;
+  int enrich_level = 0;                 // primal enrichment level (Section 3.3.2)
 
   // FETI-DP structure
   int n_P = 0, n_R = 0;               // local primal (corner) / remaining dofs
@@ -123,6 +126,14 @@ struct lat_ctx {
   std::vector<int> class_rep;         // representative cell per class
   DBuf<int> coarse_ptr, coarse_src;   // coarse matrix entries -> (cell, i, j) contributions
   DBuf<int> coarse_row, coarse_col;
+  // block-tridiagonal coarse structure (coarse DOFs grouped by the cell layer along the load
+  // axis); empty when the lattice does not give one
+  bool coarse_blocked = false;
+  int cb_n = 0, cb_m = 0;                 // number of blocks, padded block size
+  DBuf<int64_t> cb_dest;                  // coarse entry -> index in [A blocks | B blocks], -1 skip
+  DBuf<int> cb_perm;                      // block position (b*m + l) -> primal DOF or -1
+  std::vector<int32_t> h_cell_layer;
+  DBuf<double> cb_A, cb_B, cb_Dinv, cb_Einv, cb_U, cb_V, cb_T, cb_X;
 
   // selection state
   int n_r = 0;
@@ -157,11 +168,12 @@ struct lat_ctx {
   DBuf<int> flag;
   DBuf<double> red_part;            // reduction scratch
   int max_tiles = 0;
-  bool indefinite = false;
-  int64_t pcg_its_total = 0;
-  int64_t n_launch = 0;
-  int iface = 0;                      // interface preconditioner: 0 Dirichlet, 1 lumped               // kernels launched through this handle          // interface PCG iterations since the last reset
-  bool verbose = false;               // LATTICE_VERBOSE=1: per-iteration log on stderr           // some local or coarse pivot was negative
+  bool indefinite = false;              // a principal's remaining block had a negative pivot
+  bool coarse_indefinite = false;       // the coarse matrix had a negative pivot
+  int64_t pcg_its_total = 0;            // interface PCG iterations since the last reset
+  int64_t n_launch = 0;                 // kernels launched through this handle
+  int iface = 0;                        // interface preconditioner: 0 Dirichlet, 1 lumped
+  bool verbose = false;                 // LATTICE_VERBOSE=1: per-iteration log on stderr
   double *h_pinned = nullptr;          // small pinned host scratch
 
   // optional per-kernel timing: CUDA events recorded on the launching stream around the
@@ -332,5 +344,10 @@ void run_f2d(lat_ctx* h, int64_t n, const float* x, double* y);
 void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed);
 void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w);
 void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool force_all);
+void build_feti(lat_ctx* h, int level);
+void prepare_enriched(lat_ctx* h, const lat_newton_opts* o);
+void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit, int split = -1,
+               double* snap = nullptr);
+void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np);
 void run_g_to_bf16(lat_ctx* h, size_t n);
 void run_local_tc(lat_ctx* h, const double* X, double* Y);

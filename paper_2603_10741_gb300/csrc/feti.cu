@@ -334,7 +334,7 @@ __global__ void k_densify(int n_keys, const int* __restrict__ key_list, int n_cl
 constexpr int GJB = 32;
 
 __global__ void k_gj_pivot(int n, int64_t bs, int k0, int kw, double* __restrict__ A, double* __restrict__ Pinv,
-                           double* __restrict__ Cbuf, int* __restrict__ flag) {
+                           double* __restrict__ Cbuf, int* __restrict__ flag, int neg_bit) {
   __shared__ double M[GJB][GJB + 1];
   const int b = blockIdx.x;
   double* a = A + (size_t)b * bs;
@@ -351,7 +351,7 @@ __global__ void k_gj_pivot(int n, int64_t bs, int k0, int kw, double* __restrict
     const double piv = M[p][p];
     if (t == 0) {
       if (!(fabs(piv) > 0.0) || !isfinite(piv)) atomicOr(flag, 1);
-      else if (piv < 0.0) atomicOr(flag, 2);
+      else if (piv < 0.0) atomicOr(flag, neg_bit);
     }
     const double d = piv != 0.0 ? 1.0 / piv : 0.0;
     double mij = 0, mip = 0, mpj = 0;
@@ -742,11 +742,14 @@ struct SolverTmp {
 // ---------------------------------------------------------------------------------------------
 // preconditioner setup
 // ---------------------------------------------------------------------------------------------
+}  // namespace
+
 // invert `batch` n x n matrices stored with a stride of bs elements (in place).  With split in
 // (0, n) the pivot blocks stop at `split` once: the trailing block [split, n)^2 then holds the
 // Schur complement A_22 - A_21 A_11^{-1} A_12, copied to snap ([batch][n-split]^2) before the
 // sweep continues.
-void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int split = -1, double* snap = nullptr) {
+void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit, int split,
+               double* snap) {
   DBuf<double> Pinv, Cbuf, Rbuf;
   Pinv.ensure((size_t)batch * GJB * GJB);
   Cbuf.ensure((size_t)batch * n * GJB);
@@ -758,7 +761,7 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int split = 
   for (int k0 = 0; k0 < n;) {
     int kw = std::min(GJB, n - k0);
     if (split > 0 && k0 < split) kw = std::min(kw, split - k0);
-    LAT_LAUNCH(h, k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p));
+    LAT_LAUNCH(h, k_gj_pivot<<<batch, 1024, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Cbuf.p, h->flag.p, neg_bit));
     LAT_LAUNCH(h, k_gj_rows<<<dim3(div_up(n, 128), batch), 128, 0, h->stream>>>(n, bs, k0, kw, A, Pinv.p, Rbuf.p));
     {
       KernelTimer kt(h, "gj_update");
@@ -767,7 +770,7 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int split = 
     }
     LAT_CHECK_LAUNCH();
     k0 += kw;
-    if (snap && k0 == split) {
+    if (snap && k0 == split && split < n) {
       const int m = n - split;
       LAT_LAUNCH(h, k_gj_snapshot<<<dim3(div_up((int64_t)m * m, 256), batch), 256, 0, h->stream>>>(n, bs, split, A, snap));
       LAT_CHECK_LAUNCH();
@@ -779,6 +782,8 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int split = 
   Rbuf.release();
 }
 
+
+namespace {
 }  // namespace
 
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
@@ -853,7 +858,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   }
   const int nD = nR - h->n_I;
   h->SDD.ensure((size_t)nk * nD * nD);
-  gj_invert(h, h->G.p, nR, nk, gstride, h->n_I, h->SDD.p);
+  gj_invert(h, h->G.p, nR, nk, gstride, 2, h->n_I, h->SDD.p);
   h->iface = o ? o->interface_precond : 0;
   LAT_LAUNCH(h, k_phi<<<dim3(div_up(nR * nP, 128), nk), 128, 0, h->stream>>>(nR, nP, h->G.p, h->KRP.p, h->Phi.p));
   LAT_LAUNCH(h, k_schur<<<nk, 64, 0, h->stream>>>(nR, nP, h->KRP.p, h->Phi.p, h->Sloc.p));
@@ -863,18 +868,24 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   if (np > 0) {
     h->CoarseInv.ensure((size_t)np * np);
     LAT_CUDA(cudaMemsetAsync(h->CoarseInv.p, 0, (size_t)np * np * sizeof(double), h->stream));
-    const int64_t n_ent = (int64_t)h->coarse_row.n;
-    LAT_LAUNCH(h, k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p, h->coarse_col.p,
-        h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p));
-    LAT_CHECK_LAUNCH();
-    gj_invert(h, h->CoarseInv.p, (int)np, 1, np * np);
+    if (h->coarse_blocked) {
+      KernelTimer kt(h, "coarse_blocked");
+      run_coarse_blocked(h, h->Sloc.p, np);
+    } else {
+      const int64_t n_ent = (int64_t)h->coarse_row.n;
+      LAT_LAUNCH(h, k_coarse<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, np, nP, h->coarse_row.p,
+          h->coarse_col.p, h->coarse_ptr.p, h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->CoarseInv.p));
+      LAT_CHECK_LAUNCH();
+      gj_invert(h, h->CoarseInv.p, (int)np, 1, np * np, 8);
+    }
   }
   int fl = 0;
   LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));
   crep.release();
   LAT_REQUIRE(!(fl & 1), LAT_EINDEFINITE, "a local remaining-DOF matrix or the coarse matrix is singular");
-  h->indefinite = (fl & 2) != 0;
+  h->indefinite = (fl & 2) != 0;          // a principal's remaining block has a negative pivot
+  h->coarse_indefinite = (fl & 8) != 0;   // the coarse matrix has a negative pivot
   if (h->prec == LAT_MIXED_BF16) run_g_to_bf16(h, gsz);
   if (h->prec != LAT_FP64) {
     h->G32.ensure(gsz);
@@ -1209,6 +1220,23 @@ void run_axpy(lat_ctx* h, int64_t n, double a, const double* x, double* y) {
 // ---------------------------------------------------------------------------------------------
 // Newton, adjoint and the remaining entry points
 // ---------------------------------------------------------------------------------------------
+// FETI-DP setup with adaptive primal enrichment (Section 3.3.2): while the remaining block of
+// some principal, or the coarse matrix, is not positive definite, add primal nodes on every cell
+// edge, for all cells alike, rebuild the index sets and set up again; the enrichment is kept for
+// later iterations.  (With definite remaining blocks the coarse matrix loses definiteness when a
+// cell's local Schur complement does: inertia(K^s) = inertia(K_RR^s) + inertia(S^s); the edge
+// nodes tie the cells' free sides to their neighbours, which removes those modes.)
+void prepare_enriched(lat_ctx* h, const lat_newton_opts* o) {
+  run_prepare_solver(h, o);
+  while ((h->indefinite || h->coarse_indefinite) && h->enrich_level < o->max_enrich) {
+    build_feti(h, h->enrich_level + 1);
+    if (h->verbose)
+      std::fprintf(stderr, "[lattice] primal enrichment level %d: %d primal DOFs per cell, %lld coarse DOFs\n",
+                   h->enrich_level, h->n_P, (long long)h->n_primal);
+    run_prepare_solver(h, o);
+  }
+}
+
 namespace {
 
 double now_ms() {
@@ -1223,6 +1251,7 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->force_all || o->max_nr >= 1, LAT_EINVAL, "max_nr must be >= 1");
   LAT_REQUIRE(o->pcg_rtol >= 0 && o->pcg_rtol < 1, LAT_EINVAL, "pcg_rtol in [0, 1)");
   LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
+  LAT_REQUIRE(o->max_enrich >= 0 && o->max_enrich <= 6, LAT_EINVAL, "max_enrich in [0, 6]");
 }
 
 // FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
@@ -1251,6 +1280,7 @@ extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
   o->armijo_max_m = 30;
   o->pcg_rtol = 1e-2;
   o->interface_precond = 0;
+  o->max_enrich = 3;
   return LAT_OK;
 }
 
@@ -1283,7 +1313,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
       double tb = now_ms();
       R.t_select_ms += tb - ta;
-      run_prepare_solver(h, o);
+      prepare_enriched(h, o);
       double tc = now_ms();
       R.t_setup_ms += tc - tb;
       R.n_r_last = h->n_r;
@@ -1316,8 +1346,9 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       R.t_linesearch_ms += now_ms() - td;
       R.armijo_m_max = std::max(R.armijo_m_max, mm);
       if (h->verbose)
-        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d indef=%d krylov=%d pcg=%lld (rel %.1e) m=%d%s\n",
-                     it, rn, rn / r0, h->n_r, h->n_keys, (int)h->indefinite, R.krylov_its_total, (long long)h->pcg_its_total, rel, mm,
+        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d enrich=%d indef=%d/%d krylov=%d pcg=%lld (rel %.1e) m=%d%s\n",
+                     it, rn, rn / r0, h->n_r, h->n_keys, h->enrich_level, (int)h->indefinite, (int)h->coarse_indefinite,
+                     R.krylov_its_total, (long long)h->pcg_its_total, rel, mm,
                      accepted ? "" : " REJECTED");
       if (!accepted) {
         // leave u and the residual buffers consistent with u
@@ -1337,6 +1368,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     R.iterations = it;
     R.r_norm = rn;
     R.pcg_its_total = (int32_t)h->pcg_its_total;
+    R.enrich_level = h->enrich_level;
     R.converged = (rn <= o->newton_rtol * r0 || rn <= floor) ? 1 : 0;
     du.release();
     ut.release();
@@ -1350,7 +1382,7 @@ extern "C" lat_status lattice_prepare_solver(lat_handle h, const double* u, cons
   return guard(h, [&] {
     check_opts(o);
     (void)u;
-    run_prepare_solver(h, o);
+    prepare_enriched(h, o);
   });
 }
 
@@ -1421,7 +1453,7 @@ extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_
     LAT_CUDA(cudaMemsetAsync(lam.p, 0, nd * sizeof(double), h->stream));
     LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
-    run_prepare_solver(h, o);
+    prepare_enriched(h, o);
     R.n_r_last = h->n_r;
     double dn = bnorm;
     R.r0_norm = bnorm;

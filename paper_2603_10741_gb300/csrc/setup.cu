@@ -165,7 +165,7 @@ void build_pattern_and_colors(lat_ctx* h, const int* E) {
   h->color_elems.upload(ce, h->stream);
 }
 
-void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
+void build_maps(lat_ctx* h, const lat_mesh_desc* ds) {
   const int d = h->dim, nn = h->n_nodes_cell, ns = h->n_cells, nl = h->n_loc;
   const int* cn = ds->cell_nodes;
   // global node -> copies
@@ -182,27 +182,108 @@ void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
     LAT_REQUIRE(cptr[g + 1] > cptr[g], LAT_EINVAL, "global node used by no cell");
   h->copy_ptr.upload(cptr, h->stream);
   h->copy_idx.upload(cidx, h->stream);
+  h->h_cptr = cptr;
+  h->h_cidx = cidx;
+  h->h_X_ref.assign(ds->X_ref, ds->X_ref + (size_t)nn * d);
+  h->h_cell_nodes.assign(cn, cn + (size_t)ns * nn);
+  const uint8_t* fx = ds->dof_fixed;
 
-  // corners of the unit reference cell are the primal nodes (Section 3.3.1)
-  std::vector<int> corner(nn, -1);
-  int nc = 0;
+  // boundary-condition classes: cells with the same set of fixed local DOFs
+  std::map<std::vector<uint8_t>, int> cls;
+  std::vector<int> ccls(ns);
+  h->class_rep.clear();
+  for (int s = 0; s < ns; ++s) {
+    std::vector<uint8_t> mask(nl);
+    for (int k = 0; k < nl; ++k)
+      mask[k] = fx[(int64_t)cn[(size_t)s * nn + k / d] * d + k % d];
+    auto it = cls.find(mask);
+    if (it == cls.end()) {
+      int id = (int)cls.size();
+      cls[mask] = id;
+      h->class_rep.push_back(s);
+      ccls[s] = id;
+    } else {
+      ccls[s] = it->second;
+    }
+  }
+  h->n_classes = (int)cls.size();
+  h->cell_class.upload(ccls, h->stream);
+
+}
+
+// FETI-DP index sets for primal enrichment `level` (Section 3.3.2): level 0 takes the cell
+// corners as primal nodes (Section 3.3.1); level L >= 1 adds, on every edge of the unit cell
+// (the four sides in 2D, the twelve cube edges in 3D), the nodes nearest to the points
+// j / 2^L (j = 1 .. 2^L - 1) of the edge, for all cells alike.
+std::vector<int> primal_nodes(lat_ctx* h, int level) {
+  const int d = h->dim, nn = h->n_nodes_cell;
+  const std::vector<double>& X = h->h_X_ref;
+  auto is01 = [](double x) { return std::fabs(x) < 1e-12 || std::fabs(x - 1.0) < 1e-12; };
+  std::vector<int> prim(nn, -1);
+  int np = 0;
   for (int a = 0; a < nn; ++a) {
     bool c = true;
-    for (int k = 0; k < d; ++k) {
-      double x = ds->X_ref[(size_t)a * d + k];
-      c = c && (std::fabs(x) < 1e-12 || std::fabs(x - 1.0) < 1e-12);
-    }
-    if (c) corner[a] = nc++;
+    for (int k = 0; k < d; ++k) c = c && is01(X[(size_t)a * d + k]);
+    if (c) prim[a] = np++;
   }
-  LAT_REQUIRE(nc == (1 << d), LAT_EINVAL, "reference cell must have a node at every cube corner");
+  LAT_REQUIRE(np == (1 << d), LAT_EINVAL, "reference cell must have a node at every cube corner");
+  if (level <= 0) return prim;
+  // edges: the free coordinate `axis`, the fixed coordinates taking values in {0,1}
+  std::vector<int> extra;
+  for (int axis = 0; axis < d; ++axis) {
+    const int nfix = d - 1;
+    for (int combo = 0; combo < (1 << nfix); ++combo) {
+      std::vector<std::pair<double, int>> on_edge;
+      for (int a = 0; a < nn; ++a) {
+        if (prim[a] >= 0) continue;
+        bool ok = true;
+        int bit = 0;
+        for (int k = 0; k < d; ++k) {
+          if (k == axis) continue;
+          const double want = (combo >> bit++) & 1 ? 1.0 : 0.0;
+          ok = ok && std::fabs(X[(size_t)a * d + k] - want) < 1e-12;
+        }
+        if (ok) on_edge.push_back({X[(size_t)a * d + axis], a});
+      }
+      if (on_edge.empty()) continue;
+      const int parts = 1 << level;
+      for (int jj = 1; jj < parts; ++jj) {
+        const double t = (double)jj / parts;
+        int best = -1;
+        double bd = 1e300;
+        for (auto& pr : on_edge)
+          if (std::fabs(pr.first - t) < bd - 1e-12) {
+            bd = std::fabs(pr.first - t);
+            best = pr.second;
+          }
+        if (best >= 0 && prim[best] < 0) {
+          prim[best] = np++;
+          extra.push_back(best);
+        }
+      }
+    }
+  }
+  return prim;
+}
+
+void build_feti_impl(lat_ctx* h, int level) {
+  const int d = h->dim, nn = h->n_nodes_cell, ns = h->n_cells, nl = h->n_loc;
+  const int* cn = h->h_cell_nodes.data();
+  const std::vector<int>& cptr = h->h_cptr;
+  const std::vector<int>& cidx = h->h_cidx;
+  const uint8_t* fx = h->h_dof_fixed.data();
+  std::vector<int> corner = primal_nodes(h, level);
+  int nc = 0;
+  for (int a = 0; a < nn; ++a) nc += corner[a] >= 0;
+  h->enrich_level = level;
   h->corner_of_node.upload(corner, h->stream);
-  // remaining dofs ordered interior first, then the non-corner dofs on the cell boundary (the
+  // remaining dofs ordered interior first, then the non-primal dofs on the cell boundary (the
   // dual dofs): the Gauss-Jordan sweep over the interior block then leaves the dual Schur
   // complement in the trailing block (Dirichlet interface preconditioner)
   std::vector<int> rdofs, pdofs(nc * d), rpos(nl, -1);
   auto on_boundary = [&](int a) {
     for (int k = 0; k < d; ++k) {
-      double x = ds->X_ref[(size_t)a * d + k];
+      double x = h->h_X_ref[(size_t)a * d + k];
       if (std::fabs(x) < 1e-12 || std::fabs(x - 1.0) < 1e-12) return true;
     }
     return false;
@@ -227,7 +308,6 @@ void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
   h->pdofs.upload(pdofs, h->stream);
   h->rpos.upload(rpos, h->stream);
 
-  const uint8_t* fx = ds->dof_fixed;
   // free global primal DOFs, numbered by global dof
   std::vector<int64_t> pglob;
   for (int s = 0; s < ns; ++s)
@@ -318,27 +398,6 @@ void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
   h->dual_scale.upload(dsc, h->stream);
   h->n_krylov = (int64_t)nl * ns + h->n_primal + h->n_lambda;
 
-  // boundary-condition classes: cells with the same set of fixed local DOFs
-  std::map<std::vector<uint8_t>, int> cls;
-  std::vector<int> ccls(ns);
-  h->class_rep.clear();
-  for (int s = 0; s < ns; ++s) {
-    std::vector<uint8_t> mask(nl);
-    for (int k = 0; k < nl; ++k)
-      mask[k] = fx[(int64_t)cn[(size_t)s * nn + k / d] * d + k % d];
-    auto it = cls.find(mask);
-    if (it == cls.end()) {
-      int id = (int)cls.size();
-      cls[mask] = id;
-      h->class_rep.push_back(s);
-      ccls[s] = id;
-    } else {
-      ccls[s] = it->second;
-    }
-  }
-  h->n_classes = (int)cls.size();
-  h->cell_class.upload(ccls, h->stream);
-
   // coarse matrix entries (p, q) and their contributions (s, i, j), deterministic order
   std::map<std::pair<int, int>, std::vector<int>> ent;
   const int nP = h->n_P;
@@ -363,6 +422,48 @@ void build_maps_and_feti(lat_ctx* h, const lat_mesh_desc* ds) {
   h->coarse_col.upload(ccol, h->stream);
   h->coarse_ptr.upload(cptr2, h->stream);
   h->coarse_src.upload(csrc, h->stream);
+
+  // block-tridiagonal structure of the coarse matrix: a primal node belongs to the highest
+  // cell layer (along the load axis) among the cells that contain it
+  h->coarse_blocked = false;
+  if (!h->h_cell_layer.empty() && h->n_primal > 0) {
+    std::vector<int> node_blk(h->n_glob_nodes, -1);
+    for (int s = 0; s < ns; ++s)
+      for (int a = 0; a < nn; ++a)
+        if (corner[a] >= 0) {
+          int& b = node_blk[cn[(size_t)s * nn + a]];
+          b = std::max(b, (int)h->h_cell_layer[s]);
+        }
+    std::vector<int> pb(h->n_primal);
+    for (int64_t p = 0; p < h->n_primal; ++p) pb[p] = node_blk[pglob[p] / d];
+    std::vector<int> ub(pb);
+    std::sort(ub.begin(), ub.end());
+    ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
+    for (auto& b : pb) b = (int)(std::lower_bound(ub.begin(), ub.end(), b) - ub.begin());
+    const int N = (int)ub.size();
+    std::vector<int> cnt(N, 0), pos(h->n_primal);
+    for (int64_t p = 0; p < h->n_primal; ++p) pos[p] = cnt[pb[p]]++;
+    const int m = *std::max_element(cnt.begin(), cnt.end());
+    bool tri = N >= 2;
+    std::vector<int64_t> dest(crow.size(), -1);
+    const size_t mm = (size_t)m * m;
+    for (size_t e = 0; e < crow.size() && tri; ++e) {
+      const int bi = pb[crow[e]], bj = pb[ccol[e]];
+      if (std::abs(bi - bj) > 1) tri = false;
+      else if (bi == bj) dest[e] = (int64_t)(bi * mm + (size_t)pos[crow[e]] * m + pos[ccol[e]]);
+      else if (bj == bi + 1) dest[e] = (int64_t)((N + bi) * mm + (size_t)pos[crow[e]] * m + pos[ccol[e]]);
+    }
+    // worth it when the blocks are much smaller than the whole coarse problem
+    if (tri && (int64_t)m * 4 <= h->n_primal) {
+      std::vector<int> perm((size_t)N * m, -1);
+      for (int64_t p = 0; p < h->n_primal; ++p) perm[(size_t)pb[p] * m + pos[p]] = (int)p;
+      h->cb_n = N;
+      h->cb_m = m;
+      h->cb_dest.upload(dest, h->stream);
+      h->cb_perm.upload(perm, h->stream);
+      h->coarse_blocked = true;
+    }
+  }
 }
 
 __global__ void k_predictor(int64_t n, double load, const double* __restrict__ up,
@@ -393,6 +494,8 @@ __global__ void k_set_mu(int n, double mu, const double* __restrict__ th, double
 }
 
 }  // namespace
+
+void build_feti(lat_ctx* h, int level) { build_feti_impl(h, level); }
 
 static thread_local std::string g_setup_err;
 
@@ -438,7 +541,9 @@ extern "C" lat_status lattice_setup(const lat_mesh_desc* ds, lat_precision prec,
     h->dof_fixed.upload(h->h_dof_fixed, h->stream);
     h->dir_unit.upload(std::vector<double>(ds->dirichlet_unit, ds->dirichlet_unit + h->n_dof), h->stream);
     h->aff_unit.upload(std::vector<double>(ds->affine_unit, ds->affine_unit + h->n_dof), h->stream);
-    build_maps_and_feti(h, ds);
+    if (ds->cell_layer) h->h_cell_layer.assign(ds->cell_layer, ds->cell_layer + h->n_cells);
+    build_maps(h, ds);
+    build_feti_impl(h, 0);
     h->h_mu_scale.assign(h->n_cells, 1.0);
     if (ds->mu_scale) h->h_mu_scale.assign(ds->mu_scale, ds->mu_scale + h->n_cells);
     DBuf<double> th;
@@ -471,7 +576,8 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->corner_of_node); rel(h->rdofs); rel(h->pdofs); rel(h->rpos); rel(h->pidx);
   rel(h->p_copy_ptr); rel(h->p_copy); rel(h->loc_fixed); rel(h->lam_p); rel(h->lam_m);
   rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->cell_class);
-  rel(h->coarse_ptr); rel(h->coarse_src); rel(h->coarse_row); rel(h->coarse_col);
+  rel(h->coarse_ptr); rel(h->coarse_src); rel(h->cb_dest); rel(h->cb_perm); rel(h->cb_A);
+  rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->coarse_row); rel(h->coarse_col);
   rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32);
   rel(h->g_delta); rel(h->g_Z); rel(h->g_beta); rel(h->g_inf); rel(h->g_nrm2); rel(h->g_norms);
   rel(h->g_part); rel(h->g_maxres); rel(h->g_state); rel(h->g_scale);

@@ -37,7 +37,8 @@ class MeshDesc(C.Structure):
                 ("n_el_cell", C.c_int32), ("n_glob_nodes", C.c_int64),
                 ("X_ref", C.c_void_p), ("elems", C.c_void_p), ("cell_nodes", C.c_void_p),
                 ("dof_fixed", C.c_void_p), ("dirichlet_unit", C.c_void_p), ("affine_unit", C.c_void_p),
-                ("mu_scale", C.c_void_p), ("mu", C.c_double), ("lam", C.c_double)]
+                ("mu_scale", C.c_void_p), ("mu", C.c_double), ("lam", C.c_double),
+                ("cell_layer", C.c_void_p)]
 
 
 class Sizes(C.Structure):
@@ -51,7 +52,8 @@ class NewtonOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("max_nr", C.c_int32), ("force_all", C.c_int32),
                 ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("krylov_rtol", C.c_double),
                 ("krylov_max_it", C.c_int32), ("krylov_restart", C.c_int32), ("pcg_iters", C.c_int32),
-                ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32)]
+                ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32),
+                ("max_enrich", C.c_int32)]
 
 
 class NewtonReport(C.Structure):
@@ -59,7 +61,7 @@ class NewtonReport(C.Structure):
                 ("r_norm", C.c_double), ("n_r_last", C.c_int32), ("krylov_its_total", C.c_int32),
                 ("armijo_m_max", C.c_int32), ("t_residual_ms", C.c_double), ("t_select_ms", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_linesearch_ms", C.c_double),
-                ("pcg_its_total", C.c_int32)]
+                ("pcg_its_total", C.c_int32), ("enrich_level", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -145,7 +147,8 @@ def case_arrays(case):
                 cell_nodes=np.ascontiguousarray(lat.cell_nodes, dtype=np.int32),
                 dof_fixed=fixed, dirichlet_unit=dunit, affine_unit=aff,
                 mu_scale=np.ascontiguousarray(case.mu_scale, dtype=np.float64),
-                mu=float(case.mu), lam=float(case.lam), n_glob_nodes=lat.n_nodes)
+                mu=float(case.mu), lam=float(case.lam), n_glob_nodes=lat.n_nodes,
+                cell_layer=np.ascontiguousarray(np.round(lat.cell_origin[:, lat.load_axis]), dtype=np.int32))
 
 
 def greedy_select_static(T, eps, max_nr, stream=None):
@@ -184,7 +187,8 @@ class Lattice:
         desc.n_nodes_cell = a["X_ref"].shape[0]
         desc.n_el_cell = a["elems"].shape[0]
         desc.n_glob_nodes = int(a["n_glob_nodes"])
-        for f in ("X_ref", "elems", "cell_nodes", "dof_fixed", "dirichlet_unit", "affine_unit", "mu_scale"):
+        for f in ("X_ref", "elems", "cell_nodes", "dof_fixed", "dirichlet_unit", "affine_unit", "mu_scale",
+                  "cell_layer"):
             setattr(desc, f, a[f].ctypes.data if a.get(f) is not None else None)
         desc.mu, desc.lam = a["mu"], a["lam"]
         h = C.c_void_p()
@@ -193,10 +197,15 @@ class Lattice:
             raise LatticeError(st, self._lib.lattice_last_error(None).decode())
         self.h = h
         self.precision = precision
+        self.dim = a["dim"]
+
+    @property
+    def sizes(self):
+        """Current sizes.  The FETI-DP sizes (n_p_local, n_r_local, n_primal, n_lambda, n_krylov)
+        change when the solver enriches the primal set, so they are queried on every access."""
         s = Sizes()
         self._check(self._lib.lattice_sizes(self.h, C.byref(s)))
-        self.sizes = s
-        self.dim = a["dim"]
+        return s
 
     @classmethod
     def from_case(cls, case, precision=LAT_FP64, stream=None):

@@ -224,3 +224,33 @@ def test_newton_bf16_mode_ring4(L):
     err = np.linalg.norm(u.cpu().numpy() - ref[-1]) / np.linalg.norm(ref[-1])
     assert err < 1e-8, err
     lat.close()
+
+
+def test_blocked_coarse_inverse_matches_dense(L):
+    """The block-tridiagonal coarse inverse (cells grouped by layer) equals the dense one, and
+    with every cell principal K^-rom stays the exact inverse of K~ on the 8x8 ring lattice."""
+    case = latgen.make_case("ring8")
+    prob = Problem(case)
+    ud = torch.tensor(_u0(prob, 1, 0.0005, 6), device="cuda")
+    arrays = L.case_arrays(case)
+    outs = []
+    for layered in (True, False):
+        a = dict(arrays)
+        if not layered:
+            a["cell_layer"] = None
+        lat = L.Lattice(a)
+        lat.select_principal_cells(ud, 0.0, 1, force_all=True)
+        lat.lattice_prepare_solver(ud)
+        s = lat.sizes
+        rng = np.random.default_rng(7)
+        v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
+        nd = s.n_loc * s.n_cells + s.n_primal
+        v[nd:] = 0
+        Kv = lat.feti_apply(0, v)
+        Kv[nd:] = 0
+        back = lat.feti_apply(1, Kv)
+        err = (back[:nd] - v[:nd]).abs().max().item() / v[:nd].abs().max().item()
+        assert err < 1e-9, (layered, err)
+        outs.append(back[:nd].cpu().numpy())
+        lat.close()
+    assert np.abs(outs[0] - outs[1]).max() < 1e-10 * np.abs(outs[1]).max()
