@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--case", default="ring32")
-    p.add_argument("--state-step", type=int, default=4)
+    p.add_argument("--state-step", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the full-path and mixed comparisons")
     return p.parse_args()

@@ -259,7 +259,13 @@ __global__ void k_neg_masked(int64_t n, const double* __restrict__ f, const uint
 // preconditioner setup kernels
 // ---------------------------------------------------------------------------------------------
 // per cell: principal with the largest coefficient, scale c_s = sum_r alpha_r^s, key
-__global__ void k_cell_keys(int n_cells, int n_r, int force_all, const double* __restrict__ alpha,
+// per cell: the principal whose normalised snapshot is nearest (largest cosine), and the
+// least-squares scale c_s of K^s ~ c_s K^{r(s)} in the snapshot inner product.  The cosines come
+// from the greedy's coordinates: <t^s, t^{s_r}> / (|t^s| |t^{s_r}|) = sum_i beta_i^s beta_i^{s_r}
+// (the residuals of principal snapshots vanish), so c_s = |t^s| cos / |t^{s_r}|.  Principal cells
+// get themselves with c = 1.
+__global__ void k_cell_keys(int n_cells, int n_r, int force_all, const double* __restrict__ beta,
+                            const double* __restrict__ norms, const int* __restrict__ S,
                             const int* __restrict__ cls, int n_classes, int* __restrict__ key,
                             double* __restrict__ cscale) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -269,16 +275,18 @@ __global__ void k_cell_keys(int n_cells, int n_r, int force_all, const double* _
   if (force_all) {
     best = s;
   } else {
-    double bv = -DBL_MAX, sum = 0;
+    double bv = -DBL_MAX;
     for (int r = 0; r < n_r; ++r) {
-      double a = alpha[(size_t)r * n_cells + s];
-      sum += a;
-      if (a > bv) {
-        bv = a;
+      const int sr = S[r];
+      double dot = 0;
+      for (int i = 0; i <= r; ++i) dot += beta[(size_t)i * n_cells + s] * beta[(size_t)i * n_cells + sr];
+      if (dot > bv) {
+        bv = dot;
         best = r;
       }
     }
-    c = sum > 0 ? sum : (bv > 0 ? bv : 1.0);
+    const double cs = norms[s] * bv / norms[S[best]];
+    c = cs > 0 ? cs : 1.0;
   }
   key[s] = best * n_classes + cls[s];
   cscale[s] = c;
@@ -796,8 +804,8 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   // keys and scales
   h->key_of_cell.ensure(ns);
   h->c_cell.ensure(ns);
-  LAT_LAUNCH(h, k_cell_keys<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, h->n_r, h->force_all ? 1 : 0, h->alpha.p,
-                                                      h->cell_class.p, h->n_classes, h->key_of_cell.p, h->c_cell.p));
+  LAT_LAUNCH(h, k_cell_keys<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, h->n_r, h->force_all ? 1 : 0, h->g_beta.p,
+      h->g_norms.p, h->S.p, h->cell_class.p, h->n_classes, h->key_of_cell.p, h->c_cell.p));
   LAT_CHECK_LAUNCH();
   std::vector<int> keys(ns);
   LAT_CUDA(cudaMemcpyAsync(keys.data(), h->key_of_cell.p, ns * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
