@@ -209,7 +209,8 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------------------------
 KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
-           "local_segmm", "local_gemv", "local_tc", "gj_update", "krylov_orth"]
+           "local_segmm", "local_gemv", "local_tc", "gj_update", "gj_pivot", "densify", "phi_schur",
+           "coarse_blocked", "coarse_gemv", "local_segmm_dual", "local_gemv_dual", "local_tc_dual", "krylov_orth"]
 
 
 def kernel_work(name, s, n_r, n_keys, prec_bytes):

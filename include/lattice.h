@@ -201,7 +201,7 @@ typedef struct {
 } lat_newton_report;
 
 /* Default options (eps 3e-4 in 2D and 5e-3 in 3D, max_nr 256, newton_rtol 1e-8, krylov_rtol
- * 1e-10 for FP64 and 1e-6 for the mixed modes, restart 60, interface PCG to 1e-2 with at most 100
+ * 1e-10 for FP64 and 1e-6 for the mixed modes, restart 60, interface PCG to 3e-2 with at most 100
  * iterations, Armijo cap 30, Dirichlet interface preconditioner, enrichment up to level 3). */
 lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 

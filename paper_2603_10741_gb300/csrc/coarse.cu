@@ -2,16 +2,18 @@
 //
 // The coarse matrix S_PP = sum_s A_P^{sT} S^s A_P^s (Section 3.3.1) couples the primal DOFs of
 // one cell only.  Grouping the primal DOFs by the layer of cells along the load axis (a node
-// belongs to the highest layer among its cells) makes it block tridiagonal: blocks A_i on the
-// diagonal, B_i coupling block i to block i+1.  Its inverse X follows from the recurrences
+// belongs to the highest, or the lowest, layer among its cells) makes it block tridiagonal:
+// blocks A_i on the diagonal, B_i coupling block i to block i+1.  Its inverse X follows from the
+// recurrences
 //   D_0 = A_0,            D_i = A_i - B_{i-1}^T D_{i-1}^{-1} B_{i-1}       (forward)
 //   E_{N-1} = A_{N-1},    E_i = A_i - B_i E_{i+1}^{-1} B_i^T                (backward)
 //   X_ii = (D_i - B_i E_{i+1}^{-1} B_i^T)^{-1}
 //   X_ij = U_i X_{i+1,j},  U_i = -D_i^{-1} B_i          (i < j, computed wave by wave in j - i)
 //   X_ji = X_ij^T
-// at a cost of about N^2 m^3 instead of the (N m)^3 of a dense inversion.  Blocks are stored
-// padded to a common size m (identity on the padding); the result is scattered into the dense
-// inverse used by the coarse solves.
+// at a cost of about N^2 m^3 instead of the (N m)^3 of a dense inversion.  The forward and the
+// backward recurrence are independent; they advance together, one step of each per batched
+// launch.  Blocks are stored padded to a common size m (identity on the padding); the result is
+// scattered into the dense inverse used by the coarse solves.
 #include <algorithm>
 
 #include "common.cuh"
@@ -26,33 +28,35 @@ struct BatchPtrs {
   double* c[kMaxBatch];
 };
 
-// C_z = alpha op(A_z) op(B_z) + beta C_z for m x m row-major blocks (64 x 64 tiles, FP64)
-template <bool TA, bool TB>
+// C_z = alpha op(A_z) op(B_z) + beta C_z for m x m row-major blocks (T x T tiles, FP64; T = 16,
+// 32 or 64 so that small batches still spread over the SMs)
+template <bool TA, bool TB, int T>
 __global__ void __launch_bounds__(256) k_bgemm(int m, BatchPtrs P, double alpha, double beta) {
+  constexpr int U = T / 16;
   const int z = blockIdx.z;
   const double* A = P.a[z];
   const double* B = P.b[z];
   double* C = P.c[z];
-  __shared__ double As[64][33];
-  __shared__ double Bs[32][65];
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  __shared__ double As[T][33];
+  __shared__ double Bs[32][T + 1];
+  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4];
+  double acc[U][U];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < U; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
+    for (int v = 0; v < U; ++v) acc[u][v] = 0.0;
   for (int k0 = 0; k0 < m; k0 += 32) {
     __syncthreads();
-    for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
+    for (int t = threadIdx.x; t < T * 32; t += blockDim.x) {
       const int r = t / 32, c = t % 32;
       const int gi = i0 + r, gk = k0 + c;
       double v = 0.0;
       if (gi < m && gk < m) v = TA ? A[(size_t)gk * m + gi] : A[(size_t)gi * m + gk];
       As[r][c] = v;
     }
-    for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
-      const int r = t / 64, c = t % 64;
+    for (int t = threadIdx.x; t < 32 * T; t += blockDim.x) {
+      const int r = t / T, c = t % T;
       const int gk = k0 + r, gj = j0 + c;
       double v = 0.0;
       if (gk < m && gj < m) v = TB ? B[(size_t)gj * m + gk] : B[(size_t)gk * m + gj];
@@ -61,23 +65,23 @@ __global__ void __launch_bounds__(256) k_bgemm(int m, BatchPtrs P, double alpha,
     __syncthreads();
 #pragma unroll 8
     for (int l = 0; l < 32; ++l) {
-      double av[4], bv[4];
+      double av[U], bv[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) av[u] = As[ty + 16 * u][l];
+      for (int u = 0; u < U; ++u) av[u] = As[ty + 16 * u][l];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) bv[v] = Bs[l][tx + 16 * v];
+      for (int v = 0; v < U; ++v) bv[v] = Bs[l][tx + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        for (int v = 0; v < U; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < U; ++u) {
     const int gi = i0 + ty + 16 * u;
     if (gi >= m) continue;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < U; ++v) {
       const int gj = j0 + tx + 16 * v;
       if (gj >= m) continue;
       double* dst = C + (size_t)gi * m + gj;
@@ -114,9 +118,13 @@ __global__ void k_pad_identity(int nb, int m, const int* __restrict__ perm, doub
   }
 }
 
-__global__ void k_axpby_blocks(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i] + b * y[i];
+// dst_b = src_b^T for nb m x m blocks
+__global__ void k_transpose_blocks(int nb, int m, const double* __restrict__ src, double* __restrict__ dst) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t mm = (int64_t)m * m;
+  if (t >= nb * mm) return;
+  const int64_t b = t / mm, r = (t % mm) / m, c = t % m;
+  dst[b * mm + c * m + r] = src[t];
 }
 
 // dense inverse from the blocks: Inv[p][q] = X_{bp,bq}[lp][lq] (upper blocks, lower by symmetry)
@@ -146,8 +154,14 @@ void bgemm(lat_ctx* h, int m, std::vector<const double*> a, std::vector<const do
       P.b[z] = b[z0 + z];
       P.c[z] = c[z0 + z];
     }
-    dim3 grid(div_up(m, 64), div_up(m, 64), nz);
-    LAT_LAUNCH(h, (k_bgemm<TA, TB><<<grid, 256, 0, h->stream>>>(m, P, alpha, beta)));
+    const int64_t tiles64 = (int64_t)nz * div_up(m, 64) * div_up(m, 64);
+    const int64_t tiles32 = (int64_t)nz * div_up(m, 32) * div_up(m, 32);
+    if (tiles64 >= 2 * h->n_sm)
+      LAT_LAUNCH(h, (k_bgemm<TA, TB, 64><<<dim3(div_up(m, 64), div_up(m, 64), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));
+    else if (tiles32 >= h->n_sm)
+      LAT_LAUNCH(h, (k_bgemm<TA, TB, 32><<<dim3(div_up(m, 32), div_up(m, 32), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));
+    else
+      LAT_LAUNCH(h, (k_bgemm<TA, TB, 16><<<dim3(div_up(m, 16), div_up(m, 16), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));
     LAT_CHECK_LAUNCH();
   }
 }
@@ -157,50 +171,61 @@ void bgemm(lat_ctx* h, int m, std::vector<const double*> a, std::vector<const do
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
   const int N = h->cb_n, m = h->cb_m;
   const size_t mm = (size_t)m * m;
+  const int N1 = std::max(1, N - 1);
   h->cb_A.ensure(std::max<size_t>(1, (size_t)(2 * N - 1) * mm));   // A blocks then B blocks
   double* A = h->cb_A.p;
   double* Bk = A + (size_t)N * mm;
-  h->cb_Dinv.ensure(N * mm);
-  h->cb_Einv.ensure(N * mm);
-  h->cb_U.ensure(std::max(1, N - 1) * mm);
-  h->cb_T.ensure(mm);
+  h->cb_Dinv.ensure(2 * (size_t)N * mm);   // [D_0^-1 .. D_{N-1}^-1 | E_{N-1}^-1 .. E_0^-1]
+  h->cb_Einv.ensure((size_t)N1 * mm);      // B_i^T
+  h->cb_U.ensure((size_t)N1 * mm);         // D_i^-1 B_i  (= -U_i)
+  h->cb_T.ensure((size_t)N1 * mm);         // E_{i+1}^-1 B_i^T
   h->cb_X.ensure((size_t)N * N * mm);
-  double *Dinv = h->cb_Dinv.p, *Einv = h->cb_Einv.p, *U = h->cb_U.p, *T = h->cb_T.p, *X = h->cb_X.p;
+  double *DE = h->cb_Dinv.p, *Bt = h->cb_Einv.p, *U = h->cb_U.p, *T = h->cb_T.p, *X = h->cb_X.p;
+  const int64_t half = (int64_t)N * mm;    // stride from D_k^-1 to the k-th backward inverse
   auto blk = [&](double* base, int i) { return base + (size_t)i * mm; };
+  auto erev = [&](int k) { return DE + half + (size_t)k * mm; };   // E_{N-1-k}^-1
   auto xb = [&](int i, int j) { return X + ((size_t)i * N + j) * mm; };
+  auto cpy = [&](double* dst, const double* src) {
+    LAT_CUDA(cudaMemcpyAsync(dst, src, mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  };
   LAT_CUDA(cudaMemsetAsync(A, 0, (size_t)(2 * N - 1) * mm * sizeof(double), h->stream));
   const int64_t n_ent = (int64_t)h->coarse_row.n;
   LAT_LAUNCH(h, k_coarse_blocks<<<div_up(n_ent, 256), 256, 0, h->stream>>>(n_ent, h->n_P, h->coarse_ptr.p,
       h->coarse_src.p, h->key_slot.p, h->c_cell.p, h->Sloc.p, h->cb_dest.p, A));
   LAT_LAUNCH(h, k_pad_identity<<<div_up((int64_t)N * m, 256), 256, 0, h->stream>>>(N, m, h->cb_perm.p, A));
+  if (N > 1)
+    LAT_LAUNCH(h, k_transpose_blocks<<<div_up((int64_t)(N - 1) * mm, 256), 256, 0, h->stream>>>(N - 1, m, Bk, Bt));
   LAT_CHECK_LAUNCH();
   (void)S;
-  // forward: D_i (kept in X_ii until the backward sweep), D_i^{-1}, U_{i-1} = -D_{i-1}^{-1} B_{i-1}
-  LAT_CUDA(cudaMemcpyAsync(xb(0, 0), blk(A, 0), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  LAT_CUDA(cudaMemcpyAsync(blk(Dinv, 0), blk(A, 0), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  gj_invert(h, blk(Dinv, 0), m, 1, (int64_t)mm, 8);
-  for (int i = 1; i < N; ++i) {
-    bgemm<false, false>(h, m, {blk(Dinv, i - 1)}, {blk(Bk, i - 1)}, {blk(U, i - 1)}, -1.0, 0.0);
-    LAT_CUDA(cudaMemcpyAsync(xb(i, i), blk(A, i), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    bgemm<true, false>(h, m, {blk(Bk, i - 1)}, {blk(U, i - 1)}, {xb(i, i)}, 1.0, 1.0);   // A_i + B^T U
-    LAT_CUDA(cudaMemcpyAsync(blk(Dinv, i), xb(i, i), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-    gj_invert(h, blk(Dinv, i), m, 1, (int64_t)mm, 8);
+  // step 0: D_0 = A_0 (kept in X_00 until the diagonal update), E_{N-1} = A_{N-1}
+  cpy(xb(0, 0), blk(A, 0));
+  cpy(blk(DE, 0), blk(A, 0));
+  cpy(erev(0), blk(A, N - 1));
+  gj_invert(h, DE, m, 2, half, 8);
+  // step k: forward i = k and backward e = N-1-k, each pair in one batched launch
+  for (int k = 1; k < N; ++k) {
+    const int i = k, e = N - 1 - k;
+    bgemm<false, false>(h, m, {blk(DE, i - 1), erev(k - 1)}, {blk(Bk, i - 1), blk(Bt, e)}, {blk(U, i - 1), blk(T, e)},
+                        1.0, 0.0);
+    cpy(xb(i, i), blk(A, i));
+    cpy(erev(k), blk(A, e));
+    bgemm<false, false>(h, m, {blk(Bt, i - 1), blk(Bk, e)}, {blk(U, i - 1), blk(T, e)}, {xb(i, i), erev(k)}, -1.0, 1.0);
+    cpy(blk(DE, i), xb(i, i));
+    gj_invert(h, blk(DE, k), m, 2, half, 8);
   }
-  // backward: E_i^{-1}; X_ii <- D_i - B_i E_{i+1}^{-1} B_i^T
-  LAT_CUDA(cudaMemcpyAsync(blk(Einv, N - 1), blk(A, N - 1), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-  gj_invert(h, blk(Einv, N - 1), m, 1, (int64_t)mm, 8);
-  for (int i = N - 2; i >= 0; --i) {
-    bgemm<false, true>(h, m, {blk(Einv, i + 1)}, {blk(Bk, i)}, {T}, 1.0, 0.0);           // E^{-1} B^T
-    bgemm<false, false>(h, m, {blk(Bk, i)}, {T}, {xb(i, i)}, -1.0, 1.0);                // X_ii -= B T
-    if (i > 0) {
-      LAT_CUDA(cudaMemcpyAsync(blk(Einv, i), blk(A, i), mm * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
-      bgemm<false, false>(h, m, {blk(Bk, i)}, {T}, {blk(Einv, i)}, -1.0, 1.0);          // E_i
-      gj_invert(h, blk(Einv, i), m, 1, (int64_t)mm, 8);
+  // X_ii <- D_i - B_i E_{i+1}^{-1} B_i^T, then the diagonal blocks of the inverse
+  if (N > 1) {
+    std::vector<const double*> a, b;
+    std::vector<double*> c;
+    for (int i = 0; i + 1 < N; ++i) {
+      a.push_back(blk(Bk, i));
+      b.push_back(blk(T, i));
+      c.push_back(xb(i, i));
     }
+    bgemm<false, false>(h, m, a, b, c, -1.0, 1.0);
   }
-  // diagonal blocks of the inverse (batched, stride N+1 blocks)
   gj_invert(h, X, m, N, (int64_t)(N + 1) * mm, 8);
-  // upper blocks, wave by wave in d = j - i
+  // upper blocks, wave by wave in d = j - i:  X_ij = U_i X_{i+1,j} = -(D_i^-1 B_i) X_{i+1,j}
   for (int d = 1; d < N; ++d) {
     std::vector<const double*> a, b;
     std::vector<double*> c;
@@ -209,7 +234,7 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
       b.push_back(xb(j - d + 1, j));
       c.push_back(xb(j - d, j));
     }
-    bgemm<false, false>(h, m, a, b, c, 1.0, 0.0);
+    bgemm<false, false>(h, m, a, b, c, -1.0, 0.0);
   }
   const int64_t tot = (int64_t)N * m * N * m;
   LAT_LAUNCH(h, k_scatter_inverse<<<div_up(tot, 256), 256, 0, h->stream>>>(N, m, h->cb_perm.p, X, np,

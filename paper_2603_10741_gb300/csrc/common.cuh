@@ -159,7 +159,10 @@ struct lat_ctx {
   DBuf<float> G32;
   DBuf<double> SDD;                   // [n_keys][n_D][n_D] dual Schur complements
   DBuf<float> SDD32;
-  DBuf<__nv_bfloat16> G16;
+  DBuf<double> gj_P, gj_C, gj_R;      // Gauss-Jordan workspace (pivot inverse, column and row panels)
+  DBuf<int> class_rep_d;
+  DBuf<__nv_bfloat16> G16, G16d, Xb16;  // BF16 local matrices (whole, dual block), packed cell vectors
+  int g16_ld = 0, g16d_ld = 0;          // their row strides
   DBuf<double> KRP, Coarse, CoarseInv;
   DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
   DBuf<float> x32, y32;               // mixed-precision local vectors
@@ -350,4 +353,4 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
                double* snap = nullptr);
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np);
 void run_g_to_bf16(lat_ctx* h, size_t n);
-void run_local_tc(lat_ctx* h, const double* X, double* Y);
+void run_local_tc(lat_ctx* h, const double* X, double* Y, bool dual);

@@ -423,40 +423,55 @@ void build_feti_impl(lat_ctx* h, int level) {
   h->coarse_ptr.upload(cptr2, h->stream);
   h->coarse_src.upload(csrc, h->stream);
 
-  // block-tridiagonal structure of the coarse matrix: a primal node belongs to the highest
-  // cell layer (along the load axis) among the cells that contain it
+  // block-tridiagonal structure of the coarse matrix: a primal node belongs to the highest (or
+  // the lowest) cell layer along the load axis among the cells that contain it; of the two
+  // assignments the one with the smaller largest block is kept (a clamped face then adds no
+  // DOFs to its layer, so the blocks come out of equal size)
   h->coarse_blocked = false;
   if (!h->h_cell_layer.empty() && h->n_primal > 0) {
-    std::vector<int> node_blk(h->n_glob_nodes, -1);
-    for (int s = 0; s < ns; ++s)
-      for (int a = 0; a < nn; ++a)
-        if (corner[a] >= 0) {
-          int& b = node_blk[cn[(size_t)s * nn + a]];
-          b = std::max(b, (int)h->h_cell_layer[s]);
-        }
-    std::vector<int> pb(h->n_primal);
-    for (int64_t p = 0; p < h->n_primal; ++p) pb[p] = node_blk[pglob[p] / d];
-    std::vector<int> ub(pb);
-    std::sort(ub.begin(), ub.end());
-    ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
-    for (auto& b : pb) b = (int)(std::lower_bound(ub.begin(), ub.end(), b) - ub.begin());
-    const int N = (int)ub.size();
-    std::vector<int> cnt(N, 0), pos(h->n_primal);
-    for (int64_t p = 0; p < h->n_primal; ++p) pos[p] = cnt[pb[p]]++;
-    const int m = *std::max_element(cnt.begin(), cnt.end());
+    struct Blocking {
+      std::vector<int> pb, pos;
+      int N = 0, m = 0;
+    };
+    auto blocking = [&](bool highest) {
+      std::vector<int> node_blk(h->n_glob_nodes, -1);
+      for (int s = 0; s < ns; ++s)
+        for (int a = 0; a < nn; ++a)
+          if (corner[a] >= 0) {
+            int& b = node_blk[cn[(size_t)s * nn + a]];
+            const int l = (int)h->h_cell_layer[s];
+            b = b < 0 ? l : (highest ? std::max(b, l) : std::min(b, l));
+          }
+      Blocking B;
+      B.pb.resize(h->n_primal);
+      for (int64_t p = 0; p < h->n_primal; ++p) B.pb[p] = node_blk[pglob[p] / d];
+      std::vector<int> ub(B.pb);
+      std::sort(ub.begin(), ub.end());
+      ub.erase(std::unique(ub.begin(), ub.end()), ub.end());
+      for (auto& b : B.pb) b = (int)(std::lower_bound(ub.begin(), ub.end(), b) - ub.begin());
+      B.N = (int)ub.size();
+      std::vector<int> cnt(B.N, 0);
+      B.pos.resize(h->n_primal);
+      for (int64_t p = 0; p < h->n_primal; ++p) B.pos[p] = cnt[B.pb[p]]++;
+      B.m = *std::max_element(cnt.begin(), cnt.end());
+      return B;
+    };
+    Blocking hi = blocking(true), lo = blocking(false);
+    const Blocking& B = lo.m < hi.m ? lo : hi;
+    const int N = B.N, m = B.m;
     bool tri = N >= 2;
     std::vector<int64_t> dest(crow.size(), -1);
     const size_t mm = (size_t)m * m;
     for (size_t e = 0; e < crow.size() && tri; ++e) {
-      const int bi = pb[crow[e]], bj = pb[ccol[e]];
+      const int bi = B.pb[crow[e]], bj = B.pb[ccol[e]];
       if (std::abs(bi - bj) > 1) tri = false;
-      else if (bi == bj) dest[e] = (int64_t)(bi * mm + (size_t)pos[crow[e]] * m + pos[ccol[e]]);
-      else if (bj == bi + 1) dest[e] = (int64_t)((N + bi) * mm + (size_t)pos[crow[e]] * m + pos[ccol[e]]);
+      else if (bi == bj) dest[e] = (int64_t)(bi * mm + (size_t)B.pos[crow[e]] * m + B.pos[ccol[e]]);
+      else if (bj == bi + 1) dest[e] = (int64_t)((N + bi) * mm + (size_t)B.pos[crow[e]] * m + B.pos[ccol[e]]);
     }
     // worth it when the blocks are much smaller than the whole coarse problem
     if (tri && (int64_t)m * 4 <= h->n_primal) {
       std::vector<int> perm((size_t)N * m, -1);
-      for (int64_t p = 0; p < h->n_primal; ++p) perm[(size_t)pb[p] * m + pos[p]] = (int)p;
+      for (int64_t p = 0; p < h->n_primal; ++p) perm[(size_t)B.pb[p] * m + B.pos[p]] = (int)p;
       h->cb_n = N;
       h->cb_m = m;
       h->cb_dest.upload(dest, h->stream);
@@ -584,7 +599,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
   rel(h->key_of_cell); rel(h->key_slot); rel(h->perm); rel(h->seg_ptr); rel(h->tile_seg);
   rel(h->tile_c0); rel(h->key_list); rel(h->solver_int); rel(h->delta_cell); rel(h->c_cell);
-  rel(h->G); rel(h->G16); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->G16); rel(h->KRP); rel(h->Coarse);
+  rel(h->G); rel(h->G16); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->G16d); rel(h->KRP); rel(h->Coarse);
   rel(h->CoarseInv); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);

@@ -2,16 +2,17 @@
 // BF16 mixed mode: the local part of K^-rom (Eq. ifetidp_precond, Section 3.3.1) for all cells,
 //   Y[rows of cell s] = [G; Phi^T]_{key(s)} X_R^s,   G = (K_RR^r)^{-1} of the cell's principal,
 // as a segmented GEMM over cells grouped by key: one CTA computes a 128-row x 64-cell tile of
-// one key with A = the key's augmented matrix (BF16, K-major) and B = the 64 cells' remaining
-// values (FP64 -> BF16 on load, K-major), accumulating in FP32 in tensor memory.  The epilogue
-// reads the accumulator with tcgen05.ld and applies the per-cell scale 1/c_s on the G rows.
+// one key with A = the key's augmented matrix (BF16, K-major, rows padded to the K panel) and
+// B = the 64 cells' remaining values, packed once per product into a BF16 buffer in key order
+// (K-major), accumulating in FP32 in tensor memory.  The epilogue reads the accumulator with
+// tcgen05.ld and applies the per-cell scale 1/c_s on the G rows.
 //
-// Operands are staged by the CTA's threads into shared memory in the canonical no-swizzle
-// K-major layout (8-row x 16-byte core matrices; K-adjacent core matrices 128 B apart, 8-row
-// groups 1024 B apart); one elected thread issues tcgen05.mma (M = 128, N = 64, K = 16 per
-// instruction) and commits to an mbarrier that every thread waits on (bounded) before the
-// panel buffers are refilled.  Shared memory (64 KiB) and tensor memory (256 columns) are
-// allocated above what the tile needs.
+// Both operands are copied with 16-byte cp.async into shared memory in the canonical
+// no-swizzle K-major layout (8-row x 16-byte core matrices; K-adjacent core matrices 128 B
+// apart, 8-row groups 1024 B apart), two K panels in flight; one elected thread issues
+// tcgen05.mma (M = 128, N = 64, K = 16 per instruction) and commits to the stage's mbarrier,
+// which every thread waits on (bounded) before that stage is refilled.  48 KiB of shared memory
+// and 64 tensor-memory columns per CTA let four CTAs share an SM.
 #include "common.cuh"
 
 namespace {
@@ -20,10 +21,10 @@ constexpr int TM = 128;   // rows of the tile (tensor-memory lanes)
 constexpr int TN = 64;    // cells of the tile (accumulator columns)
 constexpr int TK = 64;    // K panel staged per round
 constexpr int KSTEP = 16; // K per tcgen05.mma, kind::f16
-constexpr int TMEM_COLS = 256;
-constexpr size_t SMEM_BYTES = 64 * 1024;
+constexpr int TMEM_COLS = 64;     // one FP32 accumulator column per cell of the tile
 constexpr int A_BYTES = TM * TK * 2;   // 16 KiB
 constexpr int B_BYTES = TN * TK * 2;   // 8 KiB
+constexpr size_t SMEM_BYTES = 2 * (A_BYTES + B_BYTES);   // two pipeline stages
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
 constexpr uint32_t SBO = (TK / 8) * 128;   // 8-row groups
 
@@ -66,75 +67,90 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   return false;
 }
 
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(g), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Tensor-core tile: rows [i0, i0+128) of the key's augmented matrix (BF16, row stride ldg)
+// times the 64 packed cell vectors at key-ordered positions [c0, c0+64) (BF16, row stride kp).
+// K panels of 64 flow through a 2-stage shared-memory pipeline filled by cp.async: the loads of
+// panel p+1 overlap the MMAs of panel p; a stage is refilled only after the mbarrier of the MMAs
+// that read it has completed.
 __global__ void __launch_bounds__(128)
-    k_local_tc(int n_cells, int n_R, int n_P, const __nv_bfloat16* __restrict__ G16,
-               const int* __restrict__ tile_seg, const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr,
-               const int* __restrict__ perm, const double* __restrict__ cscale, const int* __restrict__ rdofs,
-               const int* __restrict__ pdofs, const double* __restrict__ X, double* __restrict__ Y,
-               int* __restrict__ err) {
+    k_local_tc(int n_cells, int n_R, int n_P, int ldg, int kp_pad, const __nv_bfloat16* __restrict__ G16,
+               const __nv_bfloat16* __restrict__ Xb, const int* __restrict__ tile_seg,
+               const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
+               const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
+               double* __restrict__ Y, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(smem + A_BYTES);
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  __shared__ int cells[TN];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x;
-  const int key = tile_seg[tile];
-  const int c0 = tile_c0[tile];
+  const int key = tile_seg[blockIdx.x];
+  const int c0 = tile_c0[blockIdx.x];
   const int c_end = seg_ptr[key + 1];
   const int rows = n_R + n_P;
   const int i0 = blockIdx.y * TM;
-  const __nv_bfloat16* g = G16 + (size_t)key * rows * n_R;
-  if (tid < TN) {
-    const int c = c0 + tid;
-    cells[tid] = c < c_end ? perm[c] : -1;
-  }
+  const __nv_bfloat16* g = G16 + (size_t)key * rows * ldg;
+  auto stageA = [&](int st) { return smem_u32(smem) + st * (A_BYTES + B_BYTES); };
+  auto stageB = [&](int st) { return smem_u32(smem) + st * (A_BYTES + B_BYTES) + A_BYTES; };
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  const uint32_t mb = smem_u32(&mbar);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-  uint32_t parity = 0;
-  bool ok = true;
-  for (int kp = 0; kp < n_R && ok; kp += TK) {
-    // A panel: rows i0.., K kp.. (16-byte chunks of 8 bf16)
-    for (int t = tid; t < TM * (TK / 8); t += blockDim.x) {
-      const int r = t / (TK / 8), kc = t % (TK / 8);
-      const int gi = i0 + r, gk = kp + kc * 8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (gi < rows && gk < n_R) {
-        const __nv_bfloat16* src = g + (size_t)gi * n_R + gk;
-        if (gk + 8 <= n_R && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
-          v = *reinterpret_cast<const uint4*>(src);
-        } else {
-          union {
-            uint4 u;
-            __nv_bfloat16 h[8];
-          } tmp;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) tmp.h[e] = (gk + e < n_R) ? src[e] : __float2bfloat16(0.f);
-          v = tmp.u;
-        }
-      }
-      *reinterpret_cast<uint4*>(As + core_off(r, kc * 8)) = v;
+  auto load_panel = [&](int p, int st) {
+    const int kp = p * TK;
+    const uint32_t a0 = stageA(st), b0 = stageB(st);
+    for (int t = tid; t < TM * (TK / 8); t += 128) {         // A: 128 rows x 8 chunks
+      const int r = t >> 3, kc = t & 7;
+      const int gi = i0 + r;
+      const bool v = gi < rows;
+      cp_async16(a0 + 2 * core_off(r, kc * 8), v ? (const void*)(g + (size_t)gi * ldg + kp + kc * 8) : (const void*)G16,
+                 v ? 16u : 0u);
     }
-    // B panel: cells x K, converted from the FP64 saddle-point vector
-    for (int t = tid; t < TN * TK; t += blockDim.x) {
-      const int c = t % TN, kk = t / TN;
-      const int gk = kp + kk, s = cells[c];
-      const float v = (gk < n_R && s >= 0) ? (float)X[(size_t)rdofs[gk] * n_cells + s] : 0.f;
-      Bs[core_off(c, kk)] = __float2bfloat16(v);
+    for (int t = tid; t < TN * (TK / 8); t += 128) {         // B: 64 cells x 8 chunks
+      const int c = t >> 3, kc = t & 7;
+      const int pos = c0 + c;
+      const bool v = pos < c_end;
+      cp_async16(b0 + 2 * core_off(c, kc * 8),
+                 v ? (const void*)(Xb + (size_t)pos * kp_pad + kp + kc * 8) : (const void*)Xb, v ? 16u : 0u);
+    }
+    cp_async_commit();
+  };
+  const int P = (n_R + TK - 1) / TK;
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+  load_panel(0, 0);
+  for (int p = 0; p < P; ++p) {
+    const int st = p & 1;
+    if (p + 1 < P) {
+      const int nx = (p + 1) & 1;
+      if (p >= 1) {                                           // MMAs of panel p-1 read stage nx
+        const bool done = mbar_wait(smem_u32(&mbar[nx]), ph[nx]);
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
+        if (!ok) break;
+        ph[nx] ^= 1u;
+      }
+      load_panel(p + 1, nx);
+      cp_async_wait<1>();                                     // panel p has landed
+    } else {
+      cp_async_wait<0>();
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -142,24 +158,28 @@ __global__ void __launch_bounds__(128)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
       for (int ks = 0; ks < TK / KSTEP; ++ks) {
-        const uint64_t ad = make_desc(smem_u32(As) + ks * 2 * 128);
-        const uint64_t bd = make_desc(smem_u32(Bs) + ks * 2 * 128);
-        const uint32_t acc = (kp > 0 || ks > 0) ? 1u : 0u;
+        const uint64_t ad = make_desc(stageA(st) + ks * 2 * 128);
+        const uint64_t bd = make_desc(stageB(st) + ks * 2 * 128);
+        const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "{\n\t.reg .pred q;\n\t"
+            "setp.ne.b32 q, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
             "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
             : "memory");
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&mbar[st]))
                    : "memory");
     }
-    const bool done = mbar_wait(mb, parity);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(done ? 1 : 0) != 0;   // CTA-uniform decision
-    if (ok) parity ^= 1u;
   }
+  if (ok) {
+    const int last = (P - 1) & 1;
+    const bool done = mbar_wait(smem_u32(&mbar[last]), ph[last]);
+    ok = __syncthreads_and(done ? 1 : 0) != 0;
+  }
+  cp_async_wait<0>();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok) {
     // epilogue: warp w reads accumulator lanes 32w..32w+31 (tile rows), 16 columns at a time
     const int gi = i0 + warp * 32 + lane;
@@ -180,8 +200,9 @@ __global__ void __launch_bounds__(128)
       if (row_ok) {
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          const int s = cells[cb + j];
-          if (s < 0) continue;
+          const int pos = c0 + cb + j;
+          if (pos >= c_end) continue;
+          const int s = perm[pos];
           const double v = (double)__uint_as_float(r[j]);
           Y[orow * n_cells + s] = gi < n_R ? v / cscale[s] : v;
         }
@@ -189,7 +210,9 @@ __global__ void __launch_bounds__(128)
     }
   } else {
     if (tid == 0) atomicOr(err, 4);
-    mbar_wait(mb, parity);  // give any MMA still in flight a bounded chance to finish
+    // give MMAs still in flight a bounded chance to finish before the tensor memory is released
+    mbar_wait(smem_u32(&mbar[0]), ph[0]);
+    mbar_wait(smem_u32(&mbar[1]), ph[1]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -199,31 +222,85 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-__global__ void k_d2bf(int64_t n, const double* __restrict__ x, __nv_bfloat16* __restrict__ y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16((float)x[i]);
+// packed BF16 cell vectors in key order: Xb[pos][k] = X[rdofs[k]][perm[pos]], zero beyond n_R
+// (64-position x 64-k tiles through shared memory: gathered reads, 16-byte writes)
+__global__ void k_pack_x(int n_cells, int n_R, int kp_pad, const double* __restrict__ X, const int* __restrict__ perm,
+                         const int* __restrict__ rdofs, __nv_bfloat16* __restrict__ Xb) {
+  __shared__ __align__(16) __nv_bfloat16 tile[64][64 + 8];
+  const int pos0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
+  for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
+    const int kk = t / 64, pp = t % 64;                      // consecutive threads: consecutive positions
+    const int pos = pos0 + pp, k = k0 + kk;
+    float v = 0.f;
+    if (pos < n_cells && k < n_R) v = (float)X[(size_t)rdofs[k] * n_cells + perm[pos]];
+    tile[pp][kk] = __float2bfloat16(v);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
+    const int pp = t / 8, kc = t % 8;
+    const int pos = pos0 + pp;
+    if (pos < n_cells)
+      *reinterpret_cast<uint4*>(Xb + (size_t)pos * kp_pad + k0 + kc * 8) = *reinterpret_cast<const uint4*>(&tile[pp][kc * 8]);
+  }
+}
+
+// view of G (rows_v rows of n_K columns, row stride ldsrc, key stride kstride) -> BF16
+// [keys][rows_v][ld_dst], zero padded beyond n_K
+__global__ void k_g_bf16_view(int64_t keys, int rows_v, int n_K, int ldsrc, int64_t kstride,
+                              const double* __restrict__ G, int ld_dst, __nv_bfloat16* __restrict__ G16) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= keys * rows_v * ld_dst) return;
+  const int64_t row = t / ld_dst;
+  const int k = (int)(t % ld_dst);
+  const int64_t key = row / rows_v;
+  const int r = (int)(row % rows_v);
+  G16[t] = __float2bfloat16(k < n_K ? (float)G[key * kstride + (int64_t)r * ldsrc + k] : 0.f);
 }
 
 }  // namespace
 
-// BF16 copy of the augmented local matrices (after the FP64 Gauss-Jordan sweep)
+// BF16 copies of the augmented local matrices (after the FP64 Gauss-Jordan sweep), rows padded to
+// a multiple of the K panel: the whole [G; Phi^T] and its trailing dual block (rows and columns
+// from n_I on), which the interface solve multiplies
 void run_g_to_bf16(lat_ctx* h, size_t n) {
-  h->G16.ensure(n);
-  LAT_LAUNCH(h, k_d2bf<<<std::min<int64_t>((int64_t)h->n_sm * 8, ((int64_t)n + 255) / 256), 256, 0, h->stream>>>(
-                    (int64_t)n, h->G.p, h->G16.p));
+  const int nR = h->n_R, nP = h->n_P, lo0 = h->n_I;
+  const int64_t keys = (int64_t)(n / ((size_t)(nR + nP) * nR));
+  const int64_t kstride = (int64_t)(nR + nP) * nR;
+  const int ldg = (nR + TK - 1) / TK * TK;
+  h->G16.ensure((size_t)keys * (nR + nP) * ldg);
+  h->g16_ld = ldg;
+  const int64_t n1 = keys * (nR + nP) * ldg;
+  LAT_LAUNCH(h, k_g_bf16_view<<<div_up(n1, 256), 256, 0, h->stream>>>(keys, nR + nP, nR, nR, kstride, h->G.p, ldg,
+                                                                       h->G16.p));
+  const int nK = nR - lo0;
+  const int ldd = std::max(TK, (nK + TK - 1) / TK * TK);
+  h->G16d.ensure((size_t)keys * (nK + nP) * ldd);
+  h->g16d_ld = ldd;
+  const int64_t n2 = keys * (nK + nP) * ldd;
+  LAT_LAUNCH(h, k_g_bf16_view<<<div_up(n2, 256), 256, 0, h->stream>>>(keys, nK + nP, nK, nR, kstride,
+                                                                       h->G.p + (size_t)lo0 * nR + lo0, ldd, h->G16d.p));
   LAT_CHECK_LAUNCH();
 }
 
-// Y (local rows and corner rows of every cell) = [G; Phi^T] X on the tensor cores.  The tile
-// list groups cells of one key in runs of 64 (seg_bn = 64 in the mixed modes).
-void run_local_tc(lat_ctx* h, const double* X, double* Y) {
-  const int rows = h->n_R + h->n_P;
+// Y (local rows and corner rows of every cell) = [G; Phi^T] X on the tensor cores, or only the
+// dual and corner rows from the dual block when dual is set.  The tile list groups cells of one
+// key in runs of 64 (seg_bn = 64 in the mixed modes).
+void run_local_tc(lat_ctx* h, const double* X, double* Y, bool dual) {
+  const int lo0 = dual ? h->n_I : 0;
+  const int nK = h->n_R - lo0;
+  const int rows = nK + h->n_P;
+  const int kp = dual ? h->g16d_ld : h->g16_ld;
+  const __nv_bfloat16* g16 = dual ? h->G16d.p : h->G16.p;
+  const int* rd = h->rdofs.p + lo0;
+  h->Xb16.ensure((size_t)h->n_cells * h->g16_ld);
+  LAT_LAUNCH(h, k_pack_x<<<dim3(div_up(h->n_cells, 64), kp / 64), 256, 0, h->stream>>>(h->n_cells, nK, kp, X,
+                                                                                        h->perm.p, rd, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   dim3 grid(h->max_tiles, div_up(rows, TM));
-  KernelTimer kt(h, "local_tc");
-  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, h->n_R, h->n_P, h->G16.p,
+  KernelTimer kt(h, dual ? "local_tc_dual" : "local_tc");
+  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nK, h->n_P, kp, kp, g16, h->Xb16.p,
                                                                   h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p,
-                                                                  h->perm.p, h->c_cell.p, h->rdofs.p, h->pdofs.p,
-                                                                  X, Y, h->flag.p));
+                                                                  h->perm.p, h->c_cell.p, rd, h->pdofs.p, Y,
+                                                                  h->flag.p));
   LAT_CHECK_LAUNCH();
 }
