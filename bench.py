@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--state-step", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--quick", action="store_true", help="skip the full-path and mixed comparisons")
+    p.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16"],
+                   help="precision of the headline leg (fp32/bf16: mixed modes, FP64 Krylov operator)")
     return p.parse_args()
 
 
@@ -210,27 +212,60 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
            "local_segmm", "local_gemv", "local_tc", "gj_update", "gj_pivot", "densify", "phi_schur",
-           "coarse_blocked", "coarse_gemv", "local_segmm_dual", "local_gemv_dual", "local_tc_dual", "krylov_orth"]
+           "coarse_blocked", "coarse_gemv", "local_segmm_dual", "local_gemv_dual", "local_tc_dual",
+           "local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in", "krylov_orth"]
 
 
 def kernel_work(name, s, n_r, n_keys, prec_bytes):
-    """Algorithmic work per launch (bytes or flops) and its roofline (bound, peak unit).
+    """Algorithmic work per launch (bytes or flops) and its roofline kind.
 
-    local_segmm / local_gemv: the principal-block x cell-multivector product, 2 (n_R + n_P) n_R
-        flops per cell (dense local inverse and coarse restriction);
-    apply_reduced: 2 N_r nnz flops per cell (Eq. romstiffnessmatrix), bytes = X + Y + alpha;
-    apply_percell: the plain path, 2 nnz flops and 8 nnz bytes of K^s per cell;
-    residual: bytes of u gathered and f written (FP64 ALU bound: see the design doc).
+    local_segmm / local_gemv / local_tc: the principal-block x cell-multivector product,
+        2 (n_R + n_P) n_R flops per cell (dense local inverse and coarse restriction);
+    *_dual: the same on the dual block inside the interface solve, 2 (n_D + n_P) n_D per cell;
+    *_dual_in: all rows, dual columns (input supported on the dual DOFs), 2 (n_R + n_P) n_D;
+    apply_reduced: 2 N_r nnz flops per cell (Eq. romstiffnessmatrix);
+    apply_percell: the plain path, 8 nnz bytes of K^s and the two vectors per cell;
+    coarse_gemv: the explicit FP64 coarse inverse streamed once, 8 n_primal^2 bytes.
     """
     n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
-    rows = s.n_r_local + s.n_p_local
+    n_rr, n_p = s.n_r_local, s.n_p_local
+    n_d = n_rr - s.n_i_local
     if name in ("local_segmm", "local_gemv", "local_tc"):
-        return 2.0 * rows * s.n_r_local * n_s, "flops"
-    if name == "apply_reduced":
+        return 2.0 * (n_rr + n_p) * n_rr * n_s, "flops"
+    if name in ("local_segmm_dual", "local_gemv_dual", "local_tc_dual"):
+        return 2.0 * (n_d + n_p) * n_d * n_s, "flops"
+    if name in ("local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in"):
+        return 2.0 * (n_rr + n_p) * n_d * n_s, "flops"
+    if name == "apply_reduced" and n_r:
         return 2.0 * n_r * nnz * n_s, "flops"
     if name == "apply_percell":
         return 8.0 * nnz * n_s + 2 * 8.0 * n_loc * n_s, "bytes"
+    if name == "coarse_gemv":
+        return 8.0 * s.n_primal * s.n_primal + 16.0 * s.n_primal, "bytes"
     return None, None
+
+
+def kernel_rooflines(kt, s, n_r, alu_peak, hbm_peak, tensor_peak=None):
+    """Roofline entry for every timed kernel that has a work model, largest total time first."""
+    rows = []
+    for name, k in sorted(kt.items(), key=lambda kv: -kv[1]["total_ms"]):
+        work, kind = kernel_work(name, s, n_r, None, 8)
+        if work is None:
+            continue
+        avg_s = k["avg_us"] * 1e-6
+        if kind == "flops":
+            tc = name.startswith("local_tc")
+            # the local products run in the mode's precision, the Krylov operator always in FP64
+            peak = tensor_peak if tc else (alu_peak if name.startswith("local_") else FP64_PEAK_TFLOPS)
+            ach = work / avg_s / 1e12
+            rows.append({"kernel": name, "bound": "tensor" if tc else "alu", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak, "total_ms": k["total_ms"],
+                         "work_per_launch": work})
+        else:
+            ach = work / avg_s / 1e9
+            rows.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": ach / hbm_peak, "total_ms": k["total_ms"], "work_per_launch": work})
+    return rows
 
 
 def run_ours(args):
@@ -262,6 +297,9 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     def time_newton(lat, opts, steps, warmup, clocks=None, timing=False):
+        """ms per Newton iteration over `steps` timed iterations (library kernel timers off, so
+        that the interface PCG runs as CUDA-graph replays); with timing, one more untimed pass
+        with the per-kernel timers on gives the kernel breakdown."""
         u = torch.empty_like(u_start)
         reps = []
         for _ in range(warmup):
@@ -269,34 +307,43 @@ def run_ours(args):
             lat.newton_step(u, opts, max_iterations=1)
         torch.cuda.synchronize()
         barrier(ws)
-        if timing:
-            lat.lattice_set_timing(True)
         if clocks:
             clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        if clocks:
+            # headline leg: its timed region is the one a profiler started with
+            # --profile-from-start off captures (no effect without a profiler)
+            torch.cuda.profiler.start()
         e0.record(stream)
         for _ in range(steps):
             u.copy_(u_start)
             reps.append(lat.newton_step(u, opts, max_iterations=1).as_dict())
         e1.record(stream)
         torch.cuda.synchronize()
+        if clocks:
+            torch.cuda.profiler.stop()
         ck = clocks.stop(local) if clocks else None
         barrier(ws)
         ms = e0.elapsed_time(e1)
         ktimes = {}
         if timing:
+            lat.lattice_set_timing(True)
+            u.copy_(u_start)
+            lat.newton_step(u, opts, max_iterations=1)
+            torch.cuda.synchronize()
             for kname in KERNELS:
                 t, n = lat.lattice_kernel_time(kname)
                 if n:
-                    ktimes[kname] = {"total_ms": t / steps, "launches": n / steps, "avg_us": 1e3 * t / n}
+                    ktimes[kname] = {"total_ms": t, "launches": n, "avg_us": 1e3 * t / n}
             lat.lattice_set_timing(False)
         return max_over_ranks(ws, ms, dev) / steps, reps, ktimes, ck
 
     n_dof = lat_m.sizes.n_dof
     s = lat_m.sizes
     # headline: reduced path, FP64
-    lat = Lattice.from_case(case, LAT_FP64)
+    head_prec = {"fp64": LAT_FP64, "fp32": LAT_MIXED_FP32, "bf16": LAT_MIXED_BF16}[args.precision]
+    lat = Lattice.from_case(case, head_prec)
     opts = lat.lattice_default_opts()
     clocks = Clocks()
     ms_red, reps_red, kt_red, ck = time_newton(lat, opts, args.steps, args.warmup, clocks, timing=True)
@@ -304,8 +351,12 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_red, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 reduced (EIM) path", "eps": opts.eps,
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+bf16"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": {"fp64": "fp64 reduced (EIM) path",
+                                                       "fp32": "mixed: FP32 preconditioner, FP64 operator",
+                                                       "bf16": "mixed: BF16 local blocks, FP64 operator"}[args.precision],
+                   "eps": opts.eps,
                    "step": "one Newton iteration (residual, snapshots+greedy+alpha, principal tangents, "
                            "FETI-DP setup, FGMRES, Armijo, update) from the predictor of load step %d"
                            % (args.state_step + 1),
@@ -318,23 +369,17 @@ def run_ours(args):
                                                             "t_krylov_ms", "t_linesearch_ms")},
                    "kernels": kt_red},
     }
-    # dominant kernel roofline (FP64 ALU for the principal-block products)
-    dom = max(kt_red.items(), key=lambda kv: kv[1]["total_ms"])[0] if kt_red else None
-    if dom:
-        work, kind = kernel_work(dom, s, out["newton"]["n_r"], None, 8)
-        if work is not None:
-            avg_s = kt_red[dom]["avg_us"] * 1e-6
-            if kind == "flops":
-                ach = work / avg_s / 1e12
-                out["roofline"] = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                                   "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                                   "peak_source": "FP64 ALU, recipe table (1.20 measured)",
-                                   "work_per_launch": work}
-            else:
-                ach = work / avg_s / 1e9
-                out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak,
-                                   "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
-                                   "peak_source": peak_src, "work_per_launch": work}
+    # roofline of every modelled kernel; the headline entry is the one with the largest share
+    rl = kernel_rooflines(kt_red, s, out["newton"]["n_r"],
+                          FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS, hbm_peak, bf16_peak)
+    if rl:
+        top = dict(rl[0])
+        top["traffic"] = None
+        top["peak_source"] = ({"fp64": "FP64 ALU, recipe table (1.20 measured)",
+                               "fp32": "FP32 ALU, 152 SM x 128 lanes x 2 x 2.07 GHz"}.get(args.precision, peak_src)
+                              if top["bound"] == "alu" else peak_src)
+        out["roofline"] = top
+        out["kernel_rooflines"] = rl
     out["clocks"] = ck
     # launches per step, counted with the CUDA profiler on one extra step
     out["gpu_launches"] = count_launches(lat, opts, u_start) * args.steps
@@ -365,12 +410,11 @@ def run_ours(args):
                              "phase_ms": {k: reps_bf[-1][k] for k in ("t_residual_ms", "t_select_ms",
                                                                       "t_setup_ms", "t_krylov_ms")},
                              "kernels": kt_bf}
-        if "local_tc" in kt_bf:
-            work, _ = kernel_work("local_tc", s, None, None, 2)
-            ach = work / (kt_bf["local_tc"]["avg_us"] * 1e-6) / 1e12
-            out["mixed_bf16"]["tensor_roofline"] = {"kernel": "local_tc", "bound": "tensor", "achieved": ach,
-                                                    "peak": bf16_peak, "unit": "TFLOP/s",
-                                                    "frac": ach / bf16_peak, "peak_source": peak_src}
+        out["mixed_bf16"]["kernel_rooflines"] = kernel_rooflines(kt_bf, s, reps_bf[-1]["n_r_last"],
+                                                                 FP32_PEAK_TFLOPS, hbm_peak, bf16_peak)
+        out["mixed_fp32"]["kernel_rooflines"] = kernel_rooflines(kt_mix, s, reps_mix[-1]["n_r_last"],
+                                                                 FP32_PEAK_TFLOPS, hbm_peak)
+        out["fp64_full_path"]["kernel_rooflines"] = kernel_rooflines(kt_full, s, None, FP64_PEAK_TFLOPS, hbm_peak)
         lat_b.close()
     # reduced tangent action alone (selection of the benchmark state), L2 flushed between calls
     out["apply"] = bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src)

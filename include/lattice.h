@@ -87,6 +87,8 @@ typedef struct {
   int64_t n_krylov;     /* length of a saddle-point vector: n_loc*n_cells + n_primal + n_lambda */
   int32_t n_q_full;     /* quadrature points per cell, full rule */
   int32_t n_q_reduced;  /* quadrature points per cell, reduced (snapshot) rule */
+  int32_t n_i_local;    /* remaining DOFs per cell off the cell boundary; the other n_r_local -
+                           n_i_local remaining DOFs are the dual (interface) DOFs */
 } lat_sizes;
 
 /* Setup: uploads the reference cell, the maps and the boundary data, builds the local pattern,
@@ -246,9 +248,12 @@ lat_status feti_from_global(lat_handle h, const double* u_glob, double* v);
 
 /* Kernel timing: while enabled, CUDA events are recorded on the handle's stream around every
  * launch of the named kernels ("residual", "tangent_full", "tangent_reduced", "greedy_update",
- * "apply_reduced", "apply_percell", "local_segmm", "local_gemv", "gj_update", "krylov_orth").
- * lattice_set_timing clears the records; lattice_kernel_time returns the summed duration (host
- * ms) and the launch count of one name since then. */
+ * "apply_reduced", "apply_percell", "local_segmm", "local_gemv", "local_tc" and their "_dual" /
+ * "_dual_in" variants inside the interface solve, "gj_update", "gj_pivot", "densify",
+ * "phi_schur", "coarse_blocked", "coarse_gemv", "krylov_orth").  While enabled, the interface
+ * PCG iteration runs launch by launch instead of as a CUDA-graph replay, so that every launch
+ * is timed.  lattice_set_timing clears the records; lattice_kernel_time returns the summed
+ * duration (host ms) and the launch count of one name since then. */
 lat_status lattice_set_timing(lat_handle h, int32_t enable);
 lat_status lattice_kernel_time(lat_handle h, const char* name, double* total_ms, int32_t* launches);
 

@@ -161,9 +161,11 @@ struct lat_ctx {
   DBuf<float> SDD32;
   DBuf<double> gj_P, gj_C, gj_R;      // Gauss-Jordan workspace (pivot inverse, column and row panels)
   DBuf<int> class_rep_d;
-  DBuf<__nv_bfloat16> G16, G16d, Xb16;  // BF16 local matrices (whole, dual block), packed cell vectors
-  int g16_ld = 0, g16d_ld = 0;          // their row strides
+  DBuf<__nv_bfloat16> G16[3], Xb16;    // BF16 local matrices (one view per KinvMode), packed cell vectors
+  int g16_ld[3] = {0, 0, 0};           // their row strides
   DBuf<double> KRP, Coarse, CoarseInv;
+  DBuf<float> CoarseInv32;             // FP32 copy of the coarse inverse (mixed modes)
+  int64_t coarse32_ld = 0;             // its row stride (a multiple of 4)
   DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
   DBuf<float> x32, y32;               // mixed-precision local vectors
   DBuf<double> kv_tmp[6];             // saddle-point sized temporaries
@@ -182,6 +184,12 @@ struct lat_ctx {
   // optional per-kernel timing: CUDA events recorded on the launching stream around the
   // launches of named kernels (lattice_set_timing / lattice_kernel_time)
   bool timing = false;
+  // interface PCG iteration captured as a CUDA graph (dropped whenever the solver is set up)
+  cudaGraphExec_t pcg_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;    // private stream the graph is captured on
+  int pcg_exec_check = -1;              // whether the captured iteration copies its scalars out
+  int64_t pcg_graph_kernels = 0;        // kernels in one replay (added to n_launch per replay)
+  bool graphs_ok = true;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> ev;
   std::vector<cudaEvent_t> ev_pool;
 };
@@ -336,6 +344,10 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
                 double* max_res_host);
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti);
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
+inline void drop_pcg_graph(lat_ctx* h) {
+  if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
+  h->pcg_exec = nullptr;
+}
 void run_feti_operator(lat_ctx* h, const double* v, double* w);
 void run_kinv(lat_ctx* h, const double* v, double* w);
 void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, double pcg_rtol);
@@ -353,4 +365,6 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
                double* snap = nullptr);
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np);
 void run_g_to_bf16(lat_ctx* h, size_t n);
-void run_local_tc(lat_ctx* h, const double* X, double* Y, bool dual);
+// which part of the local inverse a product uses (see kinv in feti.cu)
+enum KinvMode { KINV_FULL = 0, KINV_DUAL = 1, KINV_DUAL_IN = 2 };
+void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode);

@@ -545,6 +545,14 @@ __global__ void k_d2f(int64_t n, const double* __restrict__ x, float* __restrict
     y[i] = (float)x[i];
 }
 
+// FP32 copy of a rows x cols FP64 matrix with the rows padded to ld (zeros)
+__global__ void k_d2f_pad(int64_t rows, int64_t cols, int64_t ld, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rows * ld; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / ld, c = t % ld;
+    y[t] = c < cols ? (float)x[r * cols + c] : 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // K^-rom application kernels
 // ---------------------------------------------------------------------------------------------
@@ -556,33 +564,34 @@ __device__ __forceinline__ size_t out_row(int i, int n_R, const int* __restrict_
   return (size_t)(i < n_R ? rdofs[i] : pdofs[i - n_R]);
 }
 
-// The local products below read a view of the augmented per-key matrix [G; Phi^T]: n_K rows of G
-// followed by the n_P rows of Phi^T, n_K columns, row stride ldg, key stride kstride, with the
-// view's row/column r belonging to the local DOF rdofs[r].  The whole matrix is the view with
-// n_K = n_R; inside the interface solve the inputs vanish off the dual DOFs, and the view is
-// the trailing dual block (rows and columns from n_I on: the dual DOFs are the last n_R - n_I
-// remaining DOFs).
+// The local products below read a view of the augmented per-key matrix [G; Phi^T]: n_Kr rows of
+// G followed by the n_P rows of Phi^T, n_Kc columns, row stride ldg, key stride kstride; view
+// row r < n_Kr belongs to the local DOF rr[r], view column c to rc[c].  The whole matrix is the
+// view from row and column 0 with n_Kr = n_Kc = n_R.  Inputs that vanish off the dual DOFs (the
+// last n_R - n_I remaining DOFs) need only the columns from n_I on; inside the interface solve
+// only the dual rows of the output are read as well (the trailing dual block).
 
 // plain path / many keys: one CTA per cell, warp per row
 template <typename TG>
 __global__ void __launch_bounds__(256)
-    k_local_gemv(int n_cells, int n_K, int n_P, int ldg, int64_t kstride, const TG* __restrict__ G,
-                 const int* __restrict__ slot, const double* __restrict__ cscale, const int* __restrict__ rdofs,
-                 const int* __restrict__ pdofs, const double* __restrict__ X, double* __restrict__ Y) {
+    k_local_gemv(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, const TG* __restrict__ G,
+                 const int* __restrict__ slot, const double* __restrict__ cscale, const int* __restrict__ rr,
+                 const int* __restrict__ rc, const int* __restrict__ pdofs, const double* __restrict__ X,
+                 double* __restrict__ Y) {
   extern __shared__ double xs[];
   const int s = blockIdx.x;
-  for (int k = threadIdx.x; k < n_K; k += blockDim.x) xs[k] = X[(size_t)rdofs[k] * n_cells + s];
+  for (int k = threadIdx.x; k < n_Kc; k += blockDim.x) xs[k] = X[(size_t)rc[k] * n_cells + s];
   __syncthreads();
-  const int rows = n_K + n_P;
+  const int rows = n_Kr + n_P;
   const TG* g = G + (size_t)slot[s] * kstride;
   const double inv = 1.0 / cscale[s];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < rows; i += nw) {
     const TG* gi = g + (size_t)i * ldg;
     double v = 0;
-    for (int k = lane; k < n_K; k += 32) v += (double)gi[k] * xs[k];
+    for (int k = lane; k < n_Kc; k += 32) v += (double)gi[k] * xs[k];
     v = warp_sum(v);
-    if (lane == 0) Y[out_row(i, n_K, rdofs, pdofs) * n_cells + s] = i < n_K ? v * inv : v;
+    if (lane == 0) Y[out_row(i, n_Kr, rr, pdofs) * n_cells + s] = i < n_Kr ? v * inv : v;
   }
 }
 
@@ -590,17 +599,18 @@ __global__ void __launch_bounds__(256)
 // FP32 operands accumulate in FP32 (TG = float), FP64 in FP64 (BN a multiple of 16).
 template <typename TG, int BN>
 __global__ void __launch_bounds__(256)
-    k_local_segmm(int n_cells, int n_K, int n_P, int ldg, int64_t kstride, const TG* __restrict__ G,
+    k_local_segmm(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, const TG* __restrict__ G,
                   const int* __restrict__ tile_seg,
                   const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
-                  const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
+                  const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ rc,
+                  const int* __restrict__ pdofs,
                   const double* __restrict__ X, double* __restrict__ Y) {
   constexpr int NV = BN / 16;
   const int tile = blockIdx.x;
   const int k = tile_seg[tile];
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[k + 1];
-  const int rows = n_K + n_P;
+  const int rows = n_Kr + n_P;
   const int i0 = blockIdx.y * 64;
   const TG* g = G + (size_t)k * kstride;
   __shared__ TG Gs[64][33];
@@ -616,17 +626,17 @@ __global__ void __launch_bounds__(256)
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[u][v] = TG(0);
-  for (int l0 = 0; l0 < n_K; l0 += 32) {
+  for (int l0 = 0; l0 < n_Kc; l0 += 32) {
     __syncthreads();
     for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
       const int r = t / 32, c = t % 32;
       const int gi = i0 + r, gl = l0 + c;
-      Gs[r][c] = (gi < rows && gl < n_K) ? g[(size_t)gi * ldg + gl] : TG(0);
+      Gs[r][c] = (gi < rows && gl < n_Kc) ? g[(size_t)gi * ldg + gl] : TG(0);
     }
     for (int t = threadIdx.x; t < 32 * BN; t += blockDim.x) {
       const int r = t / BN, c = t % BN;
       const int gl = l0 + r, s = cells[c];
-      Xs[r][c] = (gl < n_K && s >= 0) ? (TG)X[(size_t)rdofs[gl] * n_cells + s] : TG(0);
+      Xs[r][c] = (gl < n_Kc && s >= 0) ? (TG)X[(size_t)rc[gl] * n_cells + s] : TG(0);
     }
     __syncthreads();
 #pragma unroll 8
@@ -650,7 +660,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int gi = i0 + ty + 16 * u;
-      if (gi < rows) Y[out_row(gi, n_K, rdofs, pdofs) * n_cells + s] = gi < n_K ? (double)acc[u][v] * inv
+      if (gi < rows) Y[out_row(gi, n_Kr, rr, pdofs) * n_cells + s] = gi < n_Kr ? (double)acc[u][v] * inv
                                                                             : (double)acc[u][v];
     }
   }
@@ -660,17 +670,18 @@ __global__ void __launch_bounds__(256)
 // is the bound (two FP64 multiply-adds per clock per SM), so shared-memory traffic is free and a
 // narrow tile only trims the multiply-adds spent on the padding of short key segments.
 __global__ void __launch_bounds__(256)
-    k_local_segmm_n4(int n_cells, int n_K, int n_P, int ldg, int64_t kstride, const double* __restrict__ G,
+    k_local_segmm_n4(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, const double* __restrict__ G,
                      const int* __restrict__ tile_seg,
                      const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
-                     const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
+                     const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ rc,
+                     const int* __restrict__ pdofs,
                      const double* __restrict__ X, double* __restrict__ Y) {
   constexpr int BN = 4;
   const int tile = blockIdx.x;
   const int k = tile_seg[tile];
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[k + 1];
-  const int rows = n_K + n_P;
+  const int rows = n_Kr + n_P;
   const int i0 = blockIdx.y * 64;
   const double* g = G + (size_t)k * kstride;
   __shared__ double Gs[64][33];
@@ -682,17 +693,17 @@ __global__ void __launch_bounds__(256)
     cells[threadIdx.x] = c < c_end ? perm[c] : -1;
   }
   double acc = 0.0;
-  for (int l0 = 0; l0 < n_K; l0 += 32) {
+  for (int l0 = 0; l0 < n_Kc; l0 += 32) {
     __syncthreads();
     for (int t = threadIdx.x; t < 64 * 32; t += blockDim.x) {
       const int r = t / 32, c = t % 32;
       const int gi = i0 + r, gl = l0 + c;
-      Gs[r][c] = (gi < rows && gl < n_K) ? g[(size_t)gi * ldg + gl] : 0.0;
+      Gs[r][c] = (gi < rows && gl < n_Kc) ? g[(size_t)gi * ldg + gl] : 0.0;
     }
     if (threadIdx.x < 32 * BN) {
       const int r = threadIdx.x / BN, c = threadIdx.x % BN;
       const int gl = l0 + r, s = cells[c];
-      Xs[r][c] = (gl < n_K && s >= 0) ? X[(size_t)rdofs[gl] * n_cells + s] : 0.0;
+      Xs[r][c] = (gl < n_Kc && s >= 0) ? X[(size_t)rc[gl] * n_cells + s] : 0.0;
     }
     __syncthreads();
 #pragma unroll 8
@@ -701,7 +712,7 @@ __global__ void __launch_bounds__(256)
   const int s = cells[tx];
   const int gi = i0 + ty;
   if (s >= 0 && gi < rows)
-    Y[out_row(gi, n_K, rdofs, pdofs) * n_cells + s] = gi < n_K ? acc * (1.0 / cscale[s]) : acc;
+    Y[out_row(gi, n_Kr, rr, pdofs) * n_cells + s] = gi < n_Kr ? acc * (1.0 / cscale[s]) : acc;
 }
 
 // Dirichlet interface preconditioner, local part: y_D = c_s S_DD^{slot(s)} x_D on the dual rows
@@ -711,19 +722,21 @@ __global__ void __launch_bounds__(256)
     k_dual_schur(int n_cells, int n_I, int n_D, const TS* __restrict__ SDD, const int* __restrict__ slot,
                  const double* __restrict__ cscale, const int* __restrict__ rdofs, const double* __restrict__ X,
                  double* __restrict__ Y) {
-  extern __shared__ double xs[];
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  TS* xs = reinterpret_cast<TS*>(xs_raw);   // products and sums in TS: FP32 in the mixed modes
   const int s = blockIdx.x;
-  for (int k = threadIdx.x; k < n_D; k += blockDim.x) xs[k] = X[(size_t)rdofs[n_I + k] * n_cells + s];
+  for (int k = threadIdx.x; k < n_D; k += blockDim.x) xs[k] = (TS)X[(size_t)rdofs[n_I + k] * n_cells + s];
   __syncthreads();
   const TS* S = SDD + (size_t)slot[s] * n_D * n_D;
   const double c = cscale[s];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = wid; i < n_D; i += nw) {
     const TS* si = S + (size_t)i * n_D;
-    double v = 0;
-    for (int k = lane; k < n_D; k += 32) v += (double)si[k] * xs[k];
-    v = warp_sum(v);
-    if (lane == 0) Y[(size_t)rdofs[n_I + i] * n_cells + s] = c * v;
+    TS v = 0;
+    for (int k = lane; k < n_D; k += 32) v = fma(si[k], xs[k], v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) Y[(size_t)rdofs[n_I + i] * n_cells + s] = c * (double)v;
   }
 }
 
@@ -757,8 +770,8 @@ __global__ void k_gemv(int64_t n, const double* __restrict__ A, const double* __
 }
 
 // the same for an even n whose x fits in shared memory: x staged once per CTA (instead of once
-// per row from L2), rows streamed with 16-byte loads by a warp each, a grid of two CTAs per SM
-// striding over the rows.  HBM bound: 8 n^2 bytes per product.
+// per row from L2), each row streamed with 16-byte loads by one warp, four loads in flight per
+// lane, one row per warp so that every row starts in the first wave.  HBM bound: 8 n^2 bytes.
 __global__ void __launch_bounds__(512) k_gemv_xs(int n, const double* __restrict__ A, const double* __restrict__ x,
                                                 double* __restrict__ y) {
   extern __shared__ double xs[];
@@ -769,21 +782,53 @@ __global__ void __launch_bounds__(512) k_gemv_xs(int n, const double* __restrict
   const double2* xs2 = reinterpret_cast<const double2*>(xs);
   for (int row = blockIdx.x * nw + wid; row < n; row += gridDim.x * nw) {
     const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * n);
-    double v0 = 0, v1 = 0;
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
     int k = lane;
-    for (; k + 32 < h2; k += 64) {
-      const double2 p = __ldcs(a + k), q = __ldcs(a + k + 32);
-      const double2 xp = xs2[k], xq = xs2[k + 32];
-      v0 = fma(p.x, xp.x, fma(p.y, xp.y, v0));
-      v1 = fma(q.x, xq.x, fma(q.y, xq.y, v1));
+    for (; k + 96 < h2; k += 128) {   // four 16-byte loads in flight per lane
+      const double2 p0 = __ldcs(a + k), p1 = __ldcs(a + k + 32), p2 = __ldcs(a + k + 64), p3 = __ldcs(a + k + 96);
+      v0 = fma(p0.x, xs2[k].x, fma(p0.y, xs2[k].y, v0));
+      v1 = fma(p1.x, xs2[k + 32].x, fma(p1.y, xs2[k + 32].y, v1));
+      v2 = fma(p2.x, xs2[k + 64].x, fma(p2.y, xs2[k + 64].y, v2));
+      v3 = fma(p3.x, xs2[k + 96].x, fma(p3.y, xs2[k + 96].y, v3));
     }
     for (; k < h2; k += 32) {
       const double2 p = __ldcs(a + k);
-      const double2 xp = xs2[k];
-      v0 = fma(p.x, xp.x, fma(p.y, xp.y, v0));
+      v0 = fma(p.x, xs2[k].x, fma(p.y, xs2[k].y, v0));
     }
-    const double v = warp_sum(v0 + v1);
+    const double v = warp_sum((v0 + v1) + (v2 + v3));
     if (lane == 0) y[row] = v;
+  }
+}
+
+// FP32 copy of the coarse inverse for the mixed modes (rows padded with zeros to ld, a multiple
+// of 4): FP32 products and sums, 4 n ld bytes per product
+__global__ void __launch_bounds__(512) k_gemv_xs_f32(int n, int ld, const float* __restrict__ A,
+                                                    const double* __restrict__ x, double* __restrict__ y) {
+  extern __shared__ float xf[];
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) xf[k] = k < n ? (float)x[k] : 0.f;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int h4 = ld / 4;
+  const float4* xs4 = reinterpret_cast<const float4*>(xf);
+  for (int row = blockIdx.x * nw + wid; row < n; row += gridDim.x * nw) {
+    const float4* a = reinterpret_cast<const float4*>(A + (size_t)row * ld);
+    float v0 = 0.f, v1 = 0.f;
+    int k = lane;
+    for (; k + 32 < h4; k += 64) {
+      const float4 p = __ldcs(a + k), q = __ldcs(a + k + 32);
+      const float4 xp = xs4[k], xq = xs4[k + 32];
+      v0 = fmaf(p.x, xp.x, fmaf(p.y, xp.y, fmaf(p.z, xp.z, fmaf(p.w, xp.w, v0))));
+      v1 = fmaf(q.x, xq.x, fmaf(q.y, xq.y, fmaf(q.z, xq.z, fmaf(q.w, xq.w, v1))));
+    }
+    for (; k < h4; k += 32) {
+      const float4 p = __ldcs(a + k);
+      const float4 xp = xs4[k];
+      v0 = fmaf(p.x, xp.x, fmaf(p.y, xp.y, fmaf(p.z, xp.z, fmaf(p.w, xp.w, v0))));
+    }
+    float v = v0 + v1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) y[row] = (double)v;
   }
 }
 
@@ -909,6 +954,7 @@ namespace {
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   (void)o;
   LAT_REQUIRE(h->n_r > 0, LAT_EINVAL, "select principal cells first");
+  drop_pcg_graph(h);   // buffers and sizes below may change
   const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
   h->flag.ensure(4);
   h->red_part.ensure(4096);
@@ -1016,6 +1062,13 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
     const size_t dsz = (size_t)nk * nD * nD;
     h->SDD32.ensure(dsz);
     LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, dsz), 256, 0, h->stream>>>(dsz, h->SDD.p, h->SDD32.p));
+    if (np > 0) {
+      const int64_t ldc = (np + 3) / 4 * 4;   // rows padded to 16 bytes for vector loads
+      h->CoarseInv32.ensure((size_t)np * ldc);
+      h->coarse32_ld = ldc;
+      LAT_LAUNCH(h, k_d2f_pad<<<ew_blocks(h, np * ldc), 256, 0, h->stream>>>(np, np, ldc, h->CoarseInv.p,
+                                                                             h->CoarseInv32.p));
+    }
     LAT_CHECK_LAUNCH();
   }
   // temporaries
@@ -1054,58 +1107,70 @@ void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda) {
   LAT_CHECK_LAUNCH();
 }
 
-// x_P = S_PP^{-1} g_P with the explicit FP64 inverse of the coarse matrix
+// x_P = S_PP^{-1} g_P with the explicit inverse of the coarse matrix (computed in FP64; the mixed
+// modes apply an FP32 copy, like the rest of their preconditioner)
 void run_coarse_solve(lat_ctx* h, const double* g, double* x) {
   const int64_t np = h->n_primal;
   KernelTimer kt(h, "coarse_gemv");
   const size_t shm = (size_t)np * sizeof(double);
-  if (np % 2 == 0 && shm <= 200 * 1024) {
+  if (h->prec != LAT_FP64 && h->CoarseInv32.p && shm <= 200 * 1024) {
+    const int ldc = (int)h->coarse32_ld;
+    const size_t shf = (size_t)ldc * sizeof(float);
+    LAT_CUDA(cudaFuncSetAttribute(k_gemv_xs_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shf));
+    LAT_LAUNCH(h, k_gemv_xs_f32<<<(int)div_up(np, 16), 512, shf, h->stream>>>((int)np, ldc, h->CoarseInv32.p, g, x));
+  } else if (np % 2 == 0 && shm <= 200 * 1024) {
     LAT_CUDA(cudaFuncSetAttribute(k_gemv_xs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    const int grid = (int)std::min<int64_t>(2 * h->n_sm, div_up(np, 16));
+    const int grid = (int)div_up(np, 16);   // 16 warps per CTA, one row each
     LAT_LAUNCH(h, k_gemv_xs<<<grid, 512, shm, h->stream>>>((int)np, h->CoarseInv.p, g, x));
   } else {
     LAT_LAUNCH(h, k_gemv<<<div_up(np * 32, 256), 256, 0, h->stream>>>(np, h->CoarseInv.p, g, x));
   }
 }
 
-// w_u = K^-rom v_u  (local part and primal part; multiplier part untouched).  With dual set,
-// v_R must vanish off the dual DOFs and only the dual and corner rows of w are formed (the
-// interface operator B K^-rom B^T reads no others): the local product then takes the trailing
-// dual block of [G; Phi^T], (n_R - n_I + n_P) x (n_R - n_I) instead of (n_R + n_P) x n_R.
-void kinv(lat_ctx* h, const double* v, double* w, bool dual = false) {
+// w_u = K^-rom v_u  (local part and primal part; multiplier part untouched).
+//   KINV_FULL     any v_R; every remaining and corner row of w is formed;
+//   KINV_DUAL_IN  v_R vanishes off the dual DOFs: the product reads the dual columns only;
+//   KINV_DUAL     the same, and only the dual and corner rows of w are formed (the interface
+//                 operator B K^-rom B^T reads no others): the trailing dual block,
+//                 (n_R - n_I + n_P) x (n_R - n_I) instead of (n_R + n_P) x n_R.
+void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
   const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
-  const int lo0 = dual ? h->n_I : 0;            // first row and column of the view
-  const int nK = nR - lo0;
+  const int lo_r = mode == KINV_DUAL ? h->n_I : 0;   // first row and column of the view
+  const int lo_c = mode == KINV_FULL ? 0 : h->n_I;
+  const int nKr = nR - lo_r, nKc = nR - lo_c;
   const int64_t kstride = (int64_t)(nR + nP) * nR;
-  const size_t off = (size_t)lo0 * nR + lo0;
-  const int* rd = h->rdofs.p + lo0;
+  const size_t off = (size_t)lo_r * nR + lo_c;
+  const int* rr = h->rdofs.p + lo_r;
+  const int* rc = h->rdofs.p + lo_c;
+  static const char* const tg_gemv[3] = {"local_gemv", "local_gemv_dual", "local_gemv_dual_in"};
+  static const char* const tg_segmm[3] = {"local_segmm", "local_segmm_dual", "local_segmm_dual_in"};
   double* wl = loc_of(h, w);
   // y_R = G~ v_R and Phi^T v_R (corner rows of wl) in one product
   const bool gemv = (int64_t)h->n_keys * 8 > ns;
   const bool lo = h->prec != LAT_FP64;
   if (gemv) {
-    KernelTimer kt(h, dual ? "local_gemv_dual" : "local_gemv");
-    const size_t shm = (size_t)nK * sizeof(double);
+    KernelTimer kt(h, tg_gemv[mode]);
+    const size_t shm = (size_t)nKc * sizeof(double);
     if (lo) {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nK, nP, nR, kstride, h->G32.p + off,
-          h->key_slot.p, h->c_cell.p, rd, h->pdofs.p, v, wl));
+      LAT_LAUNCH(h, k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G32.p + off,
+          h->key_slot.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     } else {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nK, nP, nR, kstride, h->G.p + off,
-          h->key_slot.p, h->c_cell.p, rd, h->pdofs.p, v, wl));
+      LAT_LAUNCH(h, k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G.p + off,
+          h->key_slot.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     }
   } else if (h->prec == LAT_MIXED_BF16) {
-    run_local_tc(h, v, wl, dual);   // tcgen05, BF16 operands, FP32 accumulation
+    run_local_tc(h, v, wl, mode);   // tcgen05, BF16 operands, FP32 accumulation
   } else {
-    KernelTimer kt(h, dual ? "local_segmm_dual" : "local_segmm");
-    dim3 grid(h->max_tiles, div_up(nK + nP, 64));
+    KernelTimer kt(h, tg_segmm[mode]);
+    dim3 grid(h->max_tiles, div_up(nKr + nP, 64));
     if (lo)
-      LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(ns, nK, nP, nR, kstride, h->G32.p + off,
-          h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rd, h->pdofs.p, v, wl));
+      LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride,
+          h->G32.p + off, h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     else
-      LAT_LAUNCH(h, k_local_segmm_n4<<<grid, 256, 0, h->stream>>>(ns, nK, nP, nR, kstride, h->G.p + off,
-          h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rd, h->pdofs.p, v, wl));
+      LAT_LAUNCH(h, k_local_segmm_n4<<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G.p + off,
+          h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
   }
   LAT_CHECK_LAUNCH();
   if (h->n_primal) {
@@ -1117,8 +1182,8 @@ void kinv(lat_ctx* h, const double* v, double* w, bool dual = false) {
   }
   LAT_LAUNCH(h, k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl));
   if (h->n_primal) {
-    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nK), 128, 0, h->stream>>>(ns, nK, nP, (int64_t)nR * nP,
-        h->Phi.p + (size_t)lo0 * nP, h->key_slot.p, rd, h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl));
+    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nKr), 128, 0, h->stream>>>(ns, nKr, nP, (int64_t)nR * nP,
+        h->Phi.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl));
     LAT_CHECK_LAUNCH();
   }
 }
@@ -1130,7 +1195,7 @@ void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
   LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
                                                           h->dual_l2.p, nullptr, p, 1.0, t1));
   LAT_CHECK_LAUNCH();
-  kinv(h, t1, t2, true);   // t1 vanishes off the dual DOFs; only dual rows of t2 are read
+  kinv(h, t1, t2, KINV_DUAL);   // t1 vanishes off the dual DOFs; only dual rows of t2 are read
   LAT_LAUNCH(h, k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, 1.0, q, 0));
   LAT_CHECK_LAUNCH();
 }
@@ -1210,10 +1275,13 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
   double* sc = h->red_part.p + 3000;  // see k_pcg_alpha
   if (pcg_iters > 0) {
     // PCG until the preconditioned residual r^T M r has dropped by pcg_rtol^2 (checked on the
-    // host after every iteration), at most pcg_iters iterations, or until breakdown
+    // host after every iteration), at most pcg_iters iterations, or until breakdown.  One
+    // iteration updates the search direction first (p = z + beta p; p = z on the first pass, from
+    // p = 0 and beta = 0), so that every iteration is the same sequence of launches: outside the
+    // kernel-timing mode it is captured once per preconditioner setup as a CUDA graph and replayed.
     LAT_CUDA(cudaMemsetAsync(sc, 0, 8 * sizeof(double), h->stream));
     dual_precond(h, y, z, t1, t2, wloc);
-    LAT_CUDA(cudaMemcpyAsync(p, z, L * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    LAT_CUDA(cudaMemsetAsync(p, 0, L * sizeof(double), h->stream));
     dev_dot(h, L, y, z, sc);
     double rz0 = -1.0;
     if (pcg_rtol > 0) {
@@ -1222,35 +1290,80 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
       rz0 = h->h_pinned[8];
     }
     const int nb = ew_blocks(h, L);
-    int it = 0;
-    for (; it < pcg_iters; ++it) {
+    const bool check = pcg_rtol > 0;
+    auto body = [&]() {
+      LAT_LAUNCH(h, k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p));
       dual_op(h, p, q, t1, t2);
       dev_dot(h, L, p, q, sc + 1);
       LAT_LAUNCH(h, k_pcg_alpha<<<1, 1, 0, h->stream>>>(sc));
       LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, 1.0, p, x));
-      if (it + 1 == pcg_iters) break;
       LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, -1.0, q, y));
       dual_precond(h, y, z, t1, t2, wloc);
       dev_dot(h, L, y, z, sc + 2);
       LAT_LAUNCH(h, k_pcg_beta<<<1, 1, 0, h->stream>>>(sc));
-      LAT_CHECK_LAUNCH();
-      if (pcg_rtol > 0) {
+      if (check)
         LAT_CUDA(cudaMemcpyAsync(h->h_pinned + 8, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LAT_CHECK_LAUNCH();
+    };
+    bool graph = !h->timing && h->graphs_ok;
+    if (graph && (!h->pcg_exec || h->pcg_exec_check != (int)check)) {
+      if (h->pcg_exec) {
+        cudaGraphExecDestroy(h->pcg_exec);
+        h->pcg_exec = nullptr;
+      }
+      // captured on a private stream (the caller's may be the legacy default stream, which
+      // cannot be captured); replays are ordered on the handle's stream
+      const int64_t n0 = h->n_launch;
+      if (!h->cap_stream) LAT_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = h->stream;
+      cudaGraph_t g = nullptr;
+      cudaError_t e1 = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e1 == cudaSuccess) {
+        h->stream = h->cap_stream;
+        try {
+          body();
+        } catch (const LatError&) {
+          graph = false;
+        }
+        h->stream = user;
+        e1 = cudaStreamEndCapture(h->cap_stream, &g);
+      }
+      if (graph && e1 == cudaSuccess && g && cudaGraphInstantiate(&h->pcg_exec, g, 0) == cudaSuccess) {
+        h->pcg_graph_kernels = h->n_launch - n0;
+        h->pcg_exec_check = (int)check;
+      } else {
+        graph = false;
+        h->graphs_ok = false;   // this handle keeps the launch-by-launch path from now on
+        h->pcg_exec = nullptr;
+      }
+      if (g) cudaGraphDestroy(g);
+      h->n_launch = n0;
+      cudaGetLastError();
+    }
+    int it = 0;
+    for (; it < pcg_iters; ++it) {
+      if (graph) {
+        LAT_CUDA(cudaGraphLaunch(h->pcg_exec, h->stream));
+        h->n_launch += h->pcg_graph_kernels;
+      } else {
+        body();
+      }
+      if (check) {
         LAT_CUDA(cudaStreamSynchronize(h->stream));
         const double rz = h->h_pinned[8], frozen = h->h_pinned[13];
         if (frozen != 0.0 || !(rz0 > 0) || rz <= pcg_rtol * pcg_rtol * rz0) break;
       }
-      LAT_LAUNCH(h, k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p));
-      LAT_CHECK_LAUNCH();
     }
-    h->pcg_its_total += it + 1;
+    h->pcg_its_total += std::min(it + 1, pcg_iters);
   }
-  // z_l = -x ;  w_u = K^-rom (v_u - B^T z_l) = K^-rom (v_u + B^T x)
-  LAT_CUDA(cudaMemcpyAsync(t, v, (nloc + h->n_primal) * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  // z_l = -x ;  w_u = K^-rom (v_u - B^T z_l) = K^-rom v_u + K^-rom B^T x, the first term kept in t
+  // from above and the second with the dual columns only (B^T x vanishes off the dual DOFs)
+  LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
   LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, nullptr, x, 1.0, t));
+                                                          h->dual_l2.p, nullptr, x, 1.0, t1));
   LAT_CHECK_LAUNCH();
-  kinv(h, t, w);
+  kinv(h, t1, w, KINV_DUAL_IN);
+  LAT_LAUNCH(h, k_axpby<<<ew_blocks(h, nloc + h->n_primal), 256, 0, h->stream>>>(nloc + h->n_primal, 1.0, t, 1.0, w));
   LAT_LAUNCH(h, k_axpby<<<ew_blocks(h, L), 256, 0, h->stream>>>(L, -1.0, x, 0.0, la_of(h, w)));
   LAT_CHECK_LAUNCH();
 }

@@ -583,6 +583,8 @@ extern "C" lat_status lattice_setup(const lat_mesh_desc* ds, lat_precision prec,
 extern "C" lat_status lattice_destroy(lat_handle h) {
   if (!h) return LAT_OK;
   cudaStreamSynchronize(h->stream);
+  drop_pcg_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   // DBuf members free themselves through release(); walk them explicitly
   auto rel = [](auto& b) { b.release(); };
   rel(h->gradX[0]); rel(h->gradX[1]); rel(h->W[0]); rel(h->W[1]); rel(h->elems); rel(h->elem_blk);
@@ -599,8 +601,8 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
   rel(h->key_of_cell); rel(h->key_slot); rel(h->perm); rel(h->seg_ptr); rel(h->tile_seg);
   rel(h->tile_c0); rel(h->key_list); rel(h->solver_int); rel(h->delta_cell); rel(h->c_cell);
-  rel(h->G); rel(h->G16); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->G16d); rel(h->KRP); rel(h->Coarse);
-  rel(h->CoarseInv); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
+  rel(h->G); rel(h->G16[0]); rel(h->G16[1]); rel(h->G16[2]); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->KRP); rel(h->Coarse);
+  rel(h->CoarseInv); rel(h->CoarseInv32); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
@@ -632,6 +634,7 @@ extern "C" lat_status lattice_sizes(lat_handle h, lat_sizes* o) {
   o->n_krylov = h->n_krylov;
   o->n_q_full = h->nq[0] * h->n_el;
   o->n_q_reduced = h->nq[1] * h->n_el;
+  o->n_i_local = h->n_I;
   return LAT_OK;
 }
 

@@ -82,10 +82,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // panel p+1 overlap the MMAs of panel p; a stage is refilled only after the mbarrier of the MMAs
 // that read it has completed.
 __global__ void __launch_bounds__(128)
-    k_local_tc(int n_cells, int n_R, int n_P, int ldg, int kp_pad, const __nv_bfloat16* __restrict__ G16,
+    k_local_tc(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int kp_pad, const __nv_bfloat16* __restrict__ G16,
                const __nv_bfloat16* __restrict__ Xb, const int* __restrict__ tile_seg,
                const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
-               const double* __restrict__ cscale, const int* __restrict__ rdofs, const int* __restrict__ pdofs,
+               const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ pdofs,
                double* __restrict__ Y, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(128)
   const int key = tile_seg[blockIdx.x];
   const int c0 = tile_c0[blockIdx.x];
   const int c_end = seg_ptr[key + 1];
-  const int rows = n_R + n_P;
+  const int rows = n_Kr + n_P;
   const int i0 = blockIdx.y * TM;
   const __nv_bfloat16* g = G16 + (size_t)key * rows * ldg;
   auto stageA = [&](int st) { return smem_u32(smem) + st * (A_BYTES + B_BYTES); };
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(128)
     }
     cp_async_commit();
   };
-  const int P = (n_R + TK - 1) / TK;
+  const int P = (n_Kc + TK - 1) / TK;
   uint32_t ph[2] = {0u, 0u};
   bool ok = true;
   load_panel(0, 0);
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(128)
     // epilogue: warp w reads accumulator lanes 32w..32w+31 (tile rows), 16 columns at a time
     const int gi = i0 + warp * 32 + lane;
     const bool row_ok = gi < rows;
-    const size_t orow = row_ok ? (size_t)(gi < n_R ? rdofs[gi] : pdofs[gi - n_R]) : 0;
+    const size_t orow = row_ok ? (size_t)(gi < n_Kr ? rr[gi] : pdofs[gi - n_Kr]) : 0;
 #pragma unroll
     for (int cb = 0; cb < TN; cb += 16) {
       uint32_t r[16];
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(128)
           if (pos >= c_end) continue;
           const int s = perm[pos];
           const double v = (double)__uint_as_float(r[j]);
-          Y[orow * n_cells + s] = gi < n_R ? v / cscale[s] : v;
+          Y[orow * n_cells + s] = gi < n_Kr ? v / cscale[s] : v;
         }
       }
     }
@@ -259,48 +259,46 @@ __global__ void k_g_bf16_view(int64_t keys, int rows_v, int n_K, int ldsrc, int6
 
 }  // namespace
 
-// BF16 copies of the augmented local matrices (after the FP64 Gauss-Jordan sweep), rows padded to
-// a multiple of the K panel: the whole [G; Phi^T] and its trailing dual block (rows and columns
-// from n_I on), which the interface solve multiplies
+// BF16 copies of the augmented local matrices (after the FP64 Gauss-Jordan sweep) for the three
+// views of the local products (whole; dual columns; trailing dual block), rows padded to a
+// multiple of the K panel
 void run_g_to_bf16(lat_ctx* h, size_t n) {
-  const int nR = h->n_R, nP = h->n_P, lo0 = h->n_I;
+  const int nR = h->n_R, nP = h->n_P, nI = h->n_I;
   const int64_t keys = (int64_t)(n / ((size_t)(nR + nP) * nR));
   const int64_t kstride = (int64_t)(nR + nP) * nR;
-  const int ldg = (nR + TK - 1) / TK * TK;
-  h->G16.ensure((size_t)keys * (nR + nP) * ldg);
-  h->g16_ld = ldg;
-  const int64_t n1 = keys * (nR + nP) * ldg;
-  LAT_LAUNCH(h, k_g_bf16_view<<<div_up(n1, 256), 256, 0, h->stream>>>(keys, nR + nP, nR, nR, kstride, h->G.p, ldg,
-                                                                       h->G16.p));
-  const int nK = nR - lo0;
-  const int ldd = std::max(TK, (nK + TK - 1) / TK * TK);
-  h->G16d.ensure((size_t)keys * (nK + nP) * ldd);
-  h->g16d_ld = ldd;
-  const int64_t n2 = keys * (nK + nP) * ldd;
-  LAT_LAUNCH(h, k_g_bf16_view<<<div_up(n2, 256), 256, 0, h->stream>>>(keys, nK + nP, nK, nR, kstride,
-                                                                       h->G.p + (size_t)lo0 * nR + lo0, ldd, h->G16d.p));
+  for (int mode = 0; mode < 3; ++mode) {
+    const int lo_r = mode == KINV_DUAL ? nI : 0, lo_c = mode == KINV_FULL ? 0 : nI;
+    const int nKr = nR - lo_r, nKc = nR - lo_c;
+    const int ld = std::max(TK, (nKc + TK - 1) / TK * TK);
+    h->G16[mode].ensure((size_t)keys * (nKr + nP) * ld);
+    h->g16_ld[mode] = ld;
+    const int64_t cnt = keys * (nKr + nP) * ld;
+    LAT_LAUNCH(h, k_g_bf16_view<<<div_up(cnt, 256), 256, 0, h->stream>>>(keys, nKr + nP, nKc, nR, kstride,
+                                                                          h->G.p + (size_t)lo_r * nR + lo_c, ld,
+                                                                          h->G16[mode].p));
+  }
   LAT_CHECK_LAUNCH();
 }
 
-// Y (local rows and corner rows of every cell) = [G; Phi^T] X on the tensor cores, or only the
-// dual and corner rows from the dual block when dual is set.  The tile list groups cells of one
-// key in runs of 64 (seg_bn = 64 in the mixed modes).
-void run_local_tc(lat_ctx* h, const double* X, double* Y, bool dual) {
-  const int lo0 = dual ? h->n_I : 0;
-  const int nK = h->n_R - lo0;
-  const int rows = nK + h->n_P;
-  const int kp = dual ? h->g16d_ld : h->g16_ld;
-  const __nv_bfloat16* g16 = dual ? h->G16d.p : h->G16.p;
-  const int* rd = h->rdofs.p + lo0;
-  h->Xb16.ensure((size_t)h->n_cells * h->g16_ld);
-  LAT_LAUNCH(h, k_pack_x<<<dim3(div_up(h->n_cells, 64), kp / 64), 256, 0, h->stream>>>(h->n_cells, nK, kp, X,
-                                                                                        h->perm.p, rd, h->Xb16.p));
+// Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores.  The tile
+// list groups cells of one key in runs of 64 (seg_bn = 64 in the mixed modes).
+void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
+  const int lo_r = mode == KINV_DUAL ? h->n_I : 0, lo_c = mode == KINV_FULL ? 0 : h->n_I;
+  const int nKr = h->n_R - lo_r, nKc = h->n_R - lo_c;
+  const int rows = nKr + h->n_P;
+  const int kp = h->g16_ld[mode];
+  const int* rr = h->rdofs.p + lo_r;
+  const int* rc = h->rdofs.p + lo_c;
+  h->Xb16.ensure((size_t)h->n_cells * h->g16_ld[KINV_FULL]);
+  LAT_LAUNCH(h, k_pack_x<<<dim3(div_up(h->n_cells, 64), kp / 64), 256, 0, h->stream>>>(h->n_cells, nKc, kp, X,
+                                                                                        h->perm.p, rc, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   dim3 grid(h->max_tiles, div_up(rows, TM));
-  KernelTimer kt(h, dual ? "local_tc_dual" : "local_tc");
-  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nK, h->n_P, kp, kp, g16, h->Xb16.p,
-                                                                  h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p,
-                                                                  h->perm.p, h->c_cell.p, rd, h->pdofs.p, Y,
-                                                                  h->flag.p));
+  static const char* const tg[3] = {"local_tc", "local_tc_dual", "local_tc_dual_in"};
+  KernelTimer kt(h, tg[mode]);
+  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nKr, nKc, h->n_P, kp, kp,
+                                                                  h->G16[mode].p, h->Xb16.p, h->tile_seg.p,
+                                                                  h->tile_c0.p, h->seg_ptr.p, h->perm.p,
+                                                                  h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p));
   LAT_CHECK_LAUNCH();
 }

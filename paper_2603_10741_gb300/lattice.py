@@ -45,7 +45,8 @@ class Sizes(C.Structure):
     _fields_ = [("n_dof", C.c_int64), ("n_cells", C.c_int32), ("n_loc", C.c_int32),
                 ("n_blocks", C.c_int32), ("nnz", C.c_int64), ("n_r_local", C.c_int32),
                 ("n_p_local", C.c_int32), ("n_primal", C.c_int64), ("n_lambda", C.c_int64),
-                ("n_krylov", C.c_int64), ("n_q_full", C.c_int32), ("n_q_reduced", C.c_int32)]
+                ("n_krylov", C.c_int64), ("n_q_full", C.c_int32), ("n_q_reduced", C.c_int32),
+                ("n_i_local", C.c_int32)]
 
 
 class NewtonOpts(C.Structure):
