@@ -169,6 +169,7 @@ struct lat_ctx {
   DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
   DBuf<float> x32, y32;               // mixed-precision local vectors
   DBuf<double> kv_tmp[6];             // saddle-point sized temporaries
+  DBuf<double> pcg_ws;                // interface PCG vectors (5 x n_lambda)
   DBuf<double> V, Zk, Hh, gmres_small, dots_part;
   DBuf<int> flag;
   DBuf<double> red_part;            // reduction scratch

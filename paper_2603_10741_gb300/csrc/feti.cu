@@ -1073,6 +1073,7 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
   }
   // temporaries
   for (int i = 0; i < 6; ++i) h->kv_tmp[i].ensure(h->n_krylov);
+  h->pcg_ws.ensure(std::max<size_t>(1, (size_t)5 * h->n_lambda));
   h->gP.ensure(std::max<int64_t>(np, 1));
   h->xP.ensure(std::max<int64_t>(np, 1));
 }
@@ -1250,7 +1251,7 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
   double* t = h->kv_tmp[2].p;   // K^-rom v_u, later v_u - B^T z
   double* t1 = h->kv_tmp[3].p;
   double* t2 = h->kv_tmp[4].p;
-  double* pv = h->kv_tmp[5].p;  // multiplier work vectors carved from one saddle-sized buffer
+  double* pv = h->pcg_ws.p;     // five multiplier-sized work vectors
   if (L == 0) {
     kinv(h, v, w);
     return;
@@ -1262,7 +1263,7 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
   double* p = pv + 3 * L;
   double* q = pv + 4 * L;
   double* wloc = h->kv_tmp[1].p;  // dual weights (1/multiplicity) as a dense local array
-  LAT_REQUIRE(5 * L <= h->n_krylov, LAT_EINVAL, "multiplier work space too small");
+  LAT_REQUIRE((size_t)5 * L <= h->pcg_ws.n, LAT_EINVAL, "multiplier work space too small");
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
   LAT_CUDA(cudaMemsetAsync(wloc, 0, nloc * sizeof(double), h->stream));
   LAT_LAUNCH(h, k_fill_dual_weights<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_scale.p, wloc));
