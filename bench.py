@@ -216,7 +216,7 @@ KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "appl
            "local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in", "krylov_orth"]
 
 
-def kernel_work(name, s, n_r, n_keys, prec_bytes):
+def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
     """Algorithmic work per launch (bytes or flops) and its roofline kind.
 
     local_segmm / local_gemv / local_tc: the principal-block x cell-multivector product,
@@ -225,7 +225,9 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes):
     *_dual_in: all rows, dual columns (input supported on the dual DOFs), 2 (n_R + n_P) n_D;
     apply_reduced: 2 N_r nnz flops per cell (Eq. romstiffnessmatrix);
     apply_percell: the plain path, 8 nnz bytes of K^s and the two vectors per cell;
-    coarse_gemv: the explicit FP64 coarse inverse streamed once, 8 n_primal^2 bytes.
+    coarse_gemv: the explicit coarse inverse streamed once: FP64 (2 n_primal^2 flops, FP64-ALU
+        bound on GB300: one multiply-add per 8 bytes is above its FP64 rate) or, in the mixed
+        modes, its FP32 copy (4 n_primal^2 bytes, HBM bound).
     """
     n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
     n_rr, n_p = s.n_r_local, s.n_p_local
@@ -241,21 +243,24 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes):
     if name == "apply_percell":
         return 8.0 * nnz * n_s + 2 * 8.0 * n_loc * n_s, "bytes"
     if name == "coarse_gemv":
-        return 8.0 * s.n_primal * s.n_primal + 16.0 * s.n_primal, "bytes"
+        if mixed:
+            return 4.0 * s.n_primal * s.n_primal + 16.0 * s.n_primal, "bytes"
+        return 2.0 * s.n_primal * s.n_primal, "flops"
     return None, None
 
 
-def kernel_rooflines(kt, s, n_r, alu_peak, hbm_peak, tensor_peak=None):
+def kernel_rooflines(kt, s, n_r, alu_peak, hbm_peak, tensor_peak=None, mixed=False):
     """Roofline entry for every timed kernel that has a work model, largest total time first."""
     rows = []
     for name, k in sorted(kt.items(), key=lambda kv: -kv[1]["total_ms"]):
-        work, kind = kernel_work(name, s, n_r, None, 8)
+        work, kind = kernel_work(name, s, n_r, None, 8, mixed)
         if work is None:
             continue
         avg_s = k["avg_us"] * 1e-6
         if kind == "flops":
             tc = name.startswith("local_tc")
-            # the local products run in the mode's precision, the Krylov operator always in FP64
+            # the local products run in the mode's precision; the Krylov operator and the FP64
+            # coarse product in FP64
             peak = tensor_peak if tc else (alu_peak if name.startswith("local_") else FP64_PEAK_TFLOPS)
             ach = work / avg_s / 1e12
             rows.append({"kernel": name, "bound": "tensor" if tc else "alu", "achieved": ach, "peak": peak,
@@ -371,7 +376,8 @@ def run_ours(args):
     }
     # roofline of every modelled kernel; the headline entry is the one with the largest share
     rl = kernel_rooflines(kt_red, s, out["newton"]["n_r"],
-                          FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS, hbm_peak, bf16_peak)
+                          FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS, hbm_peak, bf16_peak,
+                          mixed=args.precision != "fp64")
     if rl:
         top = dict(rl[0])
         top["traffic"] = None
@@ -411,13 +417,16 @@ def run_ours(args):
                                                                       "t_setup_ms", "t_krylov_ms")},
                              "kernels": kt_bf}
         out["mixed_bf16"]["kernel_rooflines"] = kernel_rooflines(kt_bf, s, reps_bf[-1]["n_r_last"],
-                                                                 FP32_PEAK_TFLOPS, hbm_peak, bf16_peak)
+                                                                 FP32_PEAK_TFLOPS, hbm_peak, bf16_peak, mixed=True)
         out["mixed_fp32"]["kernel_rooflines"] = kernel_rooflines(kt_mix, s, reps_mix[-1]["n_r_last"],
-                                                                 FP32_PEAK_TFLOPS, hbm_peak)
+                                                                 FP32_PEAK_TFLOPS, hbm_peak, mixed=True)
         out["fp64_full_path"]["kernel_rooflines"] = kernel_rooflines(kt_full, s, None, FP64_PEAK_TFLOPS, hbm_peak)
         lat_b.close()
     # reduced tangent action alone (selection of the benchmark state), L2 flushed between calls
     out["apply"] = bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src)
+    if not args.quick and rank == 0:
+        # the 3D configuration's per-cell rows (a1-a7) at full size
+        out["strut10_kernels"] = bench_kernels_3d("strut10", 1, hbm_peak, peak_src)
     # end to end through host buffers: H2D of the state, one Newton iteration, D2H of the result
     out["e2e"] = bench_e2e(lat, opts, u_start, args, ws, dev, n_dof)
     if rank == 0 and not args.no_cpu_baseline:
@@ -435,6 +444,68 @@ def count_launches(lat, opts, u_start):
     n0 = lat.lattice_launch_count()
     lat.newton_step(u, opts, max_iterations=1)
     return lat.lattice_launch_count() - n0
+
+
+def _median_ms(fn, reps, flush=None):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def bench_kernels_3d(case_name, load_step, hbm_peak, peak_src):
+    """Rows a2 (residual), a3 (reduced-rule snapshots of every cell), a4-a6 (greedy, alpha,
+    principal tangents) and a7 (reduced apply, FP64 and FP32) on a 3D lattice at full size, from
+    the affine predictor of one load step; L2 flushed before every timed call."""
+    import torch
+    import latgen
+    from paper_2603_10741_gb300 import LAT_MIXED_FP32, Lattice
+    case = latgen.make_case(case_name)
+    lat = Lattice.from_case(case, LAT_MIXED_FP32)
+    s = lat.sizes
+    u = lat.lattice_predictor(case.top_displacement(load_step))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    eps = lat.lattice_default_opts().eps
+    stacked = s.n_loc * s.n_cells
+    res = {"workload": "%s: %d cells, %d local DOF each, %d DOF, affine predictor of load step %d"
+                       % (case_name, s.n_cells, s.n_loc, s.n_dof, load_step)}
+    t = _median_ms(lambda: lat.assemble_residual_tangent(u), 10, flush)
+    res["residual"] = {"ms": t, "gdofs": s.n_dof / t / 1e6, "qp": s.n_q_full * s.n_cells}
+    t = _median_ms(lambda: lat.assemble_residual_tangent(u, quad=1, residual=False), 10, flush)
+    res["snapshots"] = {"ms": t, "qp": s.n_q_reduced * s.n_cells,
+                        "bytes_written": 8.0 * s.nnz * s.n_cells}
+    sel = lat.select_principal_cells(u, eps, 256)
+    t = _median_ms(lambda: lat.select_principal_cells(u, eps, 256), 5, flush)
+    res["select"] = {"ms": t, "eps": eps, "n_r": sel["n_r"],
+                     "note": "snapshots + Algorithm 1 + alpha + principal tangents"}
+    n_r = sel["n_r"]
+    for tag, dt, eb in (("apply_fp64", torch.float64, 8), ("apply_fp32", torch.float32, 4)):
+        x = torch.rand((s.n_loc, s.n_cells), dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        t = _median_ms(lambda: lat.apply_reduced_tangent(x, y), 50, flush) * 1e-3
+        flops = 2.0 * n_r * s.nnz * s.n_cells
+        byts = 2.0 * eb * stacked + eb * n_r * s.n_cells + eb * n_r * s.nnz
+        alu = FP64_PEAK_TFLOPS if eb == 8 else FP32_PEAK_TFLOPS
+        res[tag] = {"us": t * 1e6, "gdofs": stacked / t / 1e9, "n_r": n_r,
+                    "hbm": {"achieved_gbs": byts / t / 1e9, "peak": hbm_peak, "frac": byts / t / 1e9 / hbm_peak,
+                            "bytes": byts, "peak_source": peak_src},
+                    "alu": {"achieved_tflops": flops / t / 1e12, "peak": alu, "frac": flops / t / 1e12 / alu},
+                    "binding": max(byts / (hbm_peak * 1e9), flops / (alu * 1e12)) / t}
+        del x, y
+    del flush
+    lat.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src):
