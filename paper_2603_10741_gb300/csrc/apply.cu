@@ -126,12 +126,12 @@ __global__ void __launch_bounds__(256)
 }
 
 // Shared-memory staged form.  A CTA is 8 warps; warp w owns local node a = 8 blockIdx.y + w and
-// its lanes own CPT x 32 consecutive cells.  Each warp stages its node's principal blocks
-// K^r_{a,:} for a chunk of RCH principals into its own slice of shared memory (so only
-// __syncwarp is needed), keeps the neighbour values x_b of its cells in registers, and for every
-// principal forms z = K^r_{a,:} x (broadcast shared loads, CPT cells per load) before the
-// alpha-weighted accumulation y += alpha_r^s z: the alpha combination is the epilogue of each
-// principal's SpMV.
+// its lanes own CPT x 32 consecutive cells (the same cells for all 8 warps).  Per chunk of RCH
+// principals the CTA stages the alpha values of its cells once, and each warp its node's
+// principal blocks K^r_{a,:} into its own slice of shared memory; the warp keeps the neighbour
+// values x_b of its cells in registers and for every principal forms z = K^r_{a,:} x
+// (broadcast shared loads, CPT cells per load) before the alpha-weighted accumulation
+// y += alpha_r^s z: the alpha combination is the epilogue of each principal's SpMV.
 template <int D>
 struct StageCfg {
   static constexpr int MAXNB = D == 2 ? 9 : 27;  // node blocks per row of a Q1 pattern
@@ -149,20 +149,22 @@ __global__ void __launch_bounds__(256)
                    const T* __restrict__ X, T* __restrict__ Y) {
   constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
   constexpr int DD = D * D;
+  constexpr int NC = 32 * CPT;                   // cells of the CTA (the same for its 8 warps)
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int a = blockIdx.y * 8 + warp;
-  if (a >= A.nn) return;                         // whole warp leaves together
-  T* ks = reinterpret_cast<T*>(sm_raw) + (size_t)warp * MAXNB * RCH * DD;
-  const int b0 = A.blk_ptr[a];
-  const int nb = A.blk_ptr[a + 1] - b0;
+  const bool active = a < A.nn;                  // idle warps still join the CTA barriers
+  T* als = reinterpret_cast<T*>(sm_raw);                                  // alpha chunk [RCH][NC]
+  T* ks = als + RCH * NC + (size_t)warp * MAXNB * RCH * DD;              // this warp's K blocks
+  const int b0 = active ? A.blk_ptr[a] : 0;
+  const int nb = active ? A.blk_ptr[a + 1] - b0 : 0;
   int cell[CPT];
   bool live[CPT];
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
-    const int c = blockIdx.x * 32 * CPT + k * 32 + lane;
-    live[k] = c < A.n_cells;
-    cell[k] = live[k] ? c : A.n_cells - 1;
+    const int c = blockIdx.x * NC + k * 32 + lane;
+    live[k] = active && c < A.n_cells;
+    cell[k] = c < A.n_cells ? c : A.n_cells - 1;
   }
   T xb[MAXNB][D][CPT];
 #pragma unroll
@@ -190,17 +192,25 @@ __global__ void __launch_bounds__(256)
     for (int k = 0; k < CPT; ++k) y[i][k] = T(0);
   for (int r0 = 0; r0 < n_r; r0 += RCH) {
     const int nr = min(RCH, n_r - r0);
-    __syncwarp();
-    for (int t = lane; t < nb * nr * DD; t += 32) {
-      const int bi = t / (nr * DD), rem = t - bi * nr * DD;
-      const int r = rem / DD, e = rem - r * DD;
-      ks[(bi * RCH + r) * DD + e] = Kp[(size_t)(r0 + r) * A.nnz + (size_t)(b0 + bi) * DD + e];
+    __syncthreads();
+    // the CTA's alpha values for this chunk of principals (one coalesced pass, no load latency
+    // inside the principal loop), then this warp's principal blocks of node a
+    for (int t = threadIdx.x; t < nr * NC; t += blockDim.x) {
+      const int r = t / NC, c = t - r * NC;
+      const int cc = blockIdx.x * NC + c;
+      als[r * NC + c] = cc < A.n_cells ? alpha[(size_t)(r0 + r) * A.n_cells + cc] : T(0);
     }
-    __syncwarp();
+    for (int bi = 0; bi < nb; ++bi)
+      for (int t = lane; t < nr * DD; t += 32) {
+        const int r = t / DD, e = t - r * DD;
+        ks[(bi * RCH + r) * DD + e] = Kp[(size_t)(r0 + r) * A.nnz + (size_t)(b0 + bi) * DD + e];
+      }
+    __syncthreads();
+    if (!active) continue;
     for (int r = 0; r < nr; ++r) {
       T al[CPT];
 #pragma unroll
-      for (int k = 0; k < CPT; ++k) al[k] = alpha[(size_t)(r0 + r) * A.n_cells + cell[k]];
+      for (int k = 0; k < CPT; ++k) al[k] = als[r * NC + k * 32 + lane];
       T z[D][CPT];
 #pragma unroll
       for (int i = 0; i < D; ++i)
@@ -245,12 +255,21 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
     KernelTimer kt(h, "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
   } else {
-    constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
-    const size_t shm = (size_t)8 * MAXNB * RCH * D * D * sizeof(T);
-    LAT_CUDA(cudaFuncSetAttribute(k_apply_staged<T, D, FETI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-    dim3 grid(div_up(h->n_cells, 32 * CPT), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_reduced");
-    LAT_LAUNCH(h, k_apply_staged<T, D, FETI><<<grid, 256, shm, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
+    if (D == 3 && sizeof(T) == 4 && h->n_r <= 2) {
+      // FP32 with few principals in 3D: the 27 neighbour blocks dominate, and a thread per
+      // (cell, node) with the alpha-combined block formed in registers needs no staging and
+      // keeps more warps in flight (measured faster; in FP64 the staged form is faster)
+      dim3 blk(32, 8);
+      dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
+      LAT_LAUNCH(h, k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
+    } else {
+      constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
+      const size_t shm = ((size_t)RCH * 32 * CPT + (size_t)8 * MAXNB * RCH * D * D) * sizeof(T);
+      LAT_CUDA(cudaFuncSetAttribute(k_apply_staged<T, D, FETI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      dim3 grid(div_up(h->n_cells, 32 * CPT), div_up(h->n_nodes_cell, 8));
+      LAT_LAUNCH(h, k_apply_staged<T, D, FETI><<<grid, 256, shm, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));
+    }
   }
   LAT_CHECK_LAUNCH();
 }

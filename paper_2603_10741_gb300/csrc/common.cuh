@@ -163,6 +163,7 @@ struct lat_ctx {
   DBuf<int> class_rep_d;
   DBuf<__nv_bfloat16> G16[3], Xb16;    // BF16 local matrices (one view per KinvMode), packed cell vectors
   int g16_ld[3] = {0, 0, 0};           // their row strides
+  int64_t g16_lo[3] = {0, 0, 0};       // offset of the low BF16 part after the high part
   DBuf<double> KRP, Coarse, CoarseInv;
   DBuf<float> CoarseInv32;             // FP32 copy of the coarse inverse (mixed modes)
   int64_t coarse32_ld = 0;             // its row stride (a multiple of 4)

@@ -782,21 +782,28 @@ __global__ void __launch_bounds__(512) k_gemv_xs(int n, const double* __restrict
   const double2* xs2 = reinterpret_cast<const double2*>(xs);
   for (int row = blockIdx.x * nw + wid; row < n; row += gridDim.x * nw) {
     const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * n);
-    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    // eight independent accumulators: the FP64 multiply-add latency is not on a chain
+    double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int k = lane;
     for (; k + 96 < h2; k += 128) {   // four 16-byte loads in flight per lane
       const double2 p0 = __ldcs(a + k), p1 = __ldcs(a + k + 32), p2 = __ldcs(a + k + 64), p3 = __ldcs(a + k + 96);
-      v0 = fma(p0.x, xs2[k].x, fma(p0.y, xs2[k].y, v0));
-      v1 = fma(p1.x, xs2[k + 32].x, fma(p1.y, xs2[k + 32].y, v1));
-      v2 = fma(p2.x, xs2[k + 64].x, fma(p2.y, xs2[k + 64].y, v2));
-      v3 = fma(p3.x, xs2[k + 96].x, fma(p3.y, xs2[k + 96].y, v3));
+      const double2 x0 = xs2[k], x1 = xs2[k + 32], x2 = xs2[k + 64], x3 = xs2[k + 96];
+      v[0] = fma(p0.x, x0.x, v[0]);
+      v[1] = fma(p0.y, x0.y, v[1]);
+      v[2] = fma(p1.x, x1.x, v[2]);
+      v[3] = fma(p1.y, x1.y, v[3]);
+      v[4] = fma(p2.x, x2.x, v[4]);
+      v[5] = fma(p2.y, x2.y, v[5]);
+      v[6] = fma(p3.x, x3.x, v[6]);
+      v[7] = fma(p3.y, x3.y, v[7]);
     }
     for (; k < h2; k += 32) {
       const double2 p = __ldcs(a + k);
-      v0 = fma(p.x, xs2[k].x, fma(p.y, xs2[k].y, v0));
+      v[0] = fma(p.x, xs2[k].x, v[0]);
+      v[1] = fma(p.y, xs2[k].y, v[1]);
     }
-    const double v = warp_sum((v0 + v1) + (v2 + v3));
-    if (lane == 0) y[row] = v;
+    const double s = warp_sum(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])));
+    if (lane == 0) y[row] = s;
   }
 }
 

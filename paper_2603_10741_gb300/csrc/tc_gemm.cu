@@ -4,8 +4,12 @@
 // as a segmented GEMM over cells grouped by key: one CTA computes a 128-row x 64-cell tile of
 // one key with A = the key's augmented matrix (BF16, K-major, rows padded to the K panel) and
 // B = the 64 cells' remaining values, packed once per product into a BF16 buffer in key order
-// (K-major), accumulating in FP32 in tensor memory.  The epilogue reads the accumulator with
-// tcgen05.ld and applies the per-cell scale 1/c_s on the G rows.
+// (K-major), accumulating in FP32 in tensor memory.  Each operand is a BF16 pair (high part and
+// the BF16 rounding of the remainder) and three products G_hi X_hi + G_hi X_lo + G_lo X_hi
+// accumulate into the same tile: ~16-bit operands, which the preconditioner needs on the
+// ill-conditioned local problems of the corner-only primal set (one BF16 rounding stalls FGMRES
+// near 1e-4 there).  The epilogue reads the accumulator with tcgen05.ld and applies the
+// per-cell scale 1/c_s on the G rows.
 //
 // Both operands are copied with 16-byte cp.async into shared memory in the canonical
 // no-swizzle K-major layout (8-row x 16-byte core matrices; K-adjacent core matrices 128 B
@@ -82,7 +86,8 @@ __device__ __forceinline__ void cp_async_wait() {
 // panel p+1 overlap the MMAs of panel p; a stage is refilled only after the mbarrier of the MMAs
 // that read it has completed.
 __global__ void __launch_bounds__(128)
-    k_local_tc(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int kp_pad, const __nv_bfloat16* __restrict__ G16,
+    k_local_tc(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int kp_pad, int64_t lo_off,
+               const __nv_bfloat16* __restrict__ G16,
                const __nv_bfloat16* __restrict__ Xb, const int* __restrict__ tile_seg,
                const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ pdofs,
@@ -114,14 +119,21 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
+  // Both operands are split into a high and a low BF16 part (G = G_hi + G_lo at lo_off elements
+  // after G_hi; X = X_hi + X_lo, row layout [X_hi | X_lo]); three passes of P K panels each,
+  // G_hi X_hi + G_hi X_lo + G_lo X_hi, accumulate into one FP32 tensor-memory tile
+  const int P = (n_Kc + TK - 1) / TK;
   auto load_panel = [&](int p, int st) {
-    const int kp = p * TK;
+    const int pass = p / P;
+    const int kp = (p - pass * P) * TK;                    // matrix column
+    const int kx = (pass == 1 ? P * TK : 0) + kp;          // packed vector column
+    const __nv_bfloat16* gp = pass == 2 ? g + lo_off : g;
     const uint32_t a0 = stageA(st), b0 = stageB(st);
     for (int t = tid; t < TM * (TK / 8); t += 128) {         // A: 128 rows x 8 chunks
       const int r = t >> 3, kc = t & 7;
       const int gi = i0 + r;
       const bool v = gi < rows;
-      cp_async16(a0 + 2 * core_off(r, kc * 8), v ? (const void*)(g + (size_t)gi * ldg + kp + kc * 8) : (const void*)G16,
+      cp_async16(a0 + 2 * core_off(r, kc * 8), v ? (const void*)(gp + (size_t)gi * ldg + kp + kc * 8) : (const void*)G16,
                  v ? 16u : 0u);
     }
     for (int t = tid; t < TN * (TK / 8); t += 128) {         // B: 64 cells x 8 chunks
@@ -129,17 +141,17 @@ __global__ void __launch_bounds__(128)
       const int pos = c0 + c;
       const bool v = pos < c_end;
       cp_async16(b0 + 2 * core_off(c, kc * 8),
-                 v ? (const void*)(Xb + (size_t)pos * kp_pad + kp + kc * 8) : (const void*)Xb, v ? 16u : 0u);
+                 v ? (const void*)(Xb + (size_t)pos * kp_pad + kx + kc * 8) : (const void*)Xb, v ? 16u : 0u);
     }
     cp_async_commit();
   };
-  const int P = (n_Kc + TK - 1) / TK;
+  const int P2 = 3 * P;
   uint32_t ph[2] = {0u, 0u};
   bool ok = true;
   load_panel(0, 0);
-  for (int p = 0; p < P; ++p) {
+  for (int p = 0; p < P2; ++p) {
     const int st = p & 1;
-    if (p + 1 < P) {
+    if (p + 1 < P2) {
       const int nx = (p + 1) & 1;
       if (p >= 1) {                                           // MMAs of panel p-1 read stage nx
         const bool done = mbar_wait(smem_u32(&mbar[nx]), ph[nx]);
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(128)
     }
   }
   if (ok) {
-    const int last = (P - 1) & 1;
+    const int last = (P2 - 1) & 1;
     const bool done = mbar_wait(smem_u32(&mbar[last]), ph[last]);
     ok = __syncthreads_and(done ? 1 : 0) != 0;
   }
@@ -222,39 +234,50 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// packed BF16 cell vectors in key order: Xb[pos][k] = X[rdofs[k]][perm[pos]], zero beyond n_R
+// packed BF16 cell vectors in key order, split into a high and a low part so that the product
+// sees the vector to ~16 mantissa bits (a single BF16 rounding of the vector, 8 bits, is
+// renewed at every preconditioner application and stalls FGMRES near 1e-4):
+//   Xb[pos][k] = hi, Xb[pos][kp + k] = lo,  hi + lo ~ X[rdofs[k]][perm[pos]],  zero beyond n_R
 // (64-position x 64-k tiles through shared memory: gathered reads, 16-byte writes)
-__global__ void k_pack_x(int n_cells, int n_R, int kp_pad, const double* __restrict__ X, const int* __restrict__ perm,
+__global__ void k_pack_x(int n_cells, int n_R, int kp, const double* __restrict__ X, const int* __restrict__ perm,
                          const int* __restrict__ rdofs, __nv_bfloat16* __restrict__ Xb) {
-  __shared__ __align__(16) __nv_bfloat16 tile[64][64 + 8];
+  __shared__ __align__(16) __nv_bfloat16 tile[2][64][64 + 8];
   const int pos0 = blockIdx.x * 64, k0 = blockIdx.y * 64;
   for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
     const int kk = t / 64, pp = t % 64;                      // consecutive threads: consecutive positions
     const int pos = pos0 + pp, k = k0 + kk;
     float v = 0.f;
     if (pos < n_cells && k < n_R) v = (float)X[(size_t)rdofs[k] * n_cells + perm[pos]];
-    tile[pp][kk] = __float2bfloat16(v);
+    const __nv_bfloat16 hi = __float2bfloat16(v);
+    tile[0][pp][kk] = hi;
+    tile[1][pp][kk] = __float2bfloat16(v - __bfloat162float(hi));
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 64 * 8; t += blockDim.x) {
-    const int pp = t / 8, kc = t % 8;
+  for (int t = threadIdx.x; t < 2 * 64 * 8; t += blockDim.x) {
+    const int part = t / 512, pp = (t / 8) % 64, kc = t % 8;
     const int pos = pos0 + pp;
     if (pos < n_cells)
-      *reinterpret_cast<uint4*>(Xb + (size_t)pos * kp_pad + k0 + kc * 8) = *reinterpret_cast<const uint4*>(&tile[pp][kc * 8]);
+      *reinterpret_cast<uint4*>(Xb + (size_t)pos * 2 * kp + part * kp + k0 + kc * 8) =
+          *reinterpret_cast<const uint4*>(&tile[part][pp][kc * 8]);
   }
 }
 
-// view of G (rows_v rows of n_K columns, row stride ldsrc, key stride kstride) -> BF16
-// [keys][rows_v][ld_dst], zero padded beyond n_K
+// view of G (rows_v rows of n_K columns, row stride ldsrc, key stride kstride) -> BF16 high
+// part [keys][rows_v][ld_dst] followed by the BF16 low part (G - hi) of the same shape, zero
+// padded beyond n_K
 __global__ void k_g_bf16_view(int64_t keys, int rows_v, int n_K, int ldsrc, int64_t kstride,
                               const double* __restrict__ G, int ld_dst, __nv_bfloat16* __restrict__ G16) {
+  const int64_t n = keys * rows_v * ld_dst;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= keys * rows_v * ld_dst) return;
+  if (t >= n) return;
   const int64_t row = t / ld_dst;
   const int k = (int)(t % ld_dst);
   const int64_t key = row / rows_v;
   const int r = (int)(row % rows_v);
-  G16[t] = __float2bfloat16(k < n_K ? (float)G[key * kstride + (int64_t)r * ldsrc + k] : 0.f);
+  const float v = k < n_K ? (float)G[key * kstride + (int64_t)r * ldsrc + k] : 0.f;
+  const __nv_bfloat16 hi = __float2bfloat16(v);
+  G16[t] = hi;
+  G16[n + t] = __float2bfloat16(v - __bfloat162float(hi));
 }
 
 }  // namespace
@@ -270,8 +293,9 @@ void run_g_to_bf16(lat_ctx* h, size_t n) {
     const int lo_r = mode == KINV_DUAL ? nI : 0, lo_c = mode == KINV_FULL ? 0 : nI;
     const int nKr = nR - lo_r, nKc = nR - lo_c;
     const int ld = std::max(TK, (nKc + TK - 1) / TK * TK);
-    h->G16[mode].ensure((size_t)keys * (nKr + nP) * ld);
+    h->G16[mode].ensure((size_t)2 * keys * (nKr + nP) * ld);   // high and low parts
     h->g16_ld[mode] = ld;
+    h->g16_lo[mode] = keys * (nKr + nP) * ld;
     const int64_t cnt = keys * (nKr + nP) * ld;
     LAT_LAUNCH(h, k_g_bf16_view<<<div_up(cnt, 256), 256, 0, h->stream>>>(keys, nKr + nP, nKc, nR, kstride,
                                                                           h->G.p + (size_t)lo_r * nR + lo_c, ld,
@@ -289,14 +313,15 @@ void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
   const int kp = h->g16_ld[mode];
   const int* rr = h->rdofs.p + lo_r;
   const int* rc = h->rdofs.p + lo_c;
-  h->Xb16.ensure((size_t)h->n_cells * h->g16_ld[KINV_FULL]);
+  h->Xb16.ensure((size_t)h->n_cells * 2 * h->g16_ld[KINV_FULL]);
   LAT_LAUNCH(h, k_pack_x<<<dim3(div_up(h->n_cells, 64), kp / 64), 256, 0, h->stream>>>(h->n_cells, nKc, kp, X,
                                                                                         h->perm.p, rc, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
   dim3 grid(h->max_tiles, div_up(rows, TM));
   static const char* const tg[3] = {"local_tc", "local_tc_dual", "local_tc_dual_in"};
   KernelTimer kt(h, tg[mode]);
-  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nKr, nKc, h->n_P, kp, kp,
+  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nKr, nKc, h->n_P, kp, 2 * kp,
+                                                                  h->g16_lo[mode],
                                                                   h->G16[mode].p, h->Xb16.p, h->tile_seg.p,
                                                                   h->tile_c0.p, h->seg_ptr.p, h->perm.p,
                                                                   h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p));

@@ -211,3 +211,43 @@ def test_full_size_ring32_sampled(L):
     Y_ref = OR.reduced_apply(prob.cell, Kp, al[:, cells], X[:, cells])
     assert _rel(Y[:, cells], Y_ref) < 1e-10
     lat.close()
+
+
+def test_full_size_strut10_sampled(L):
+    """The 10x10x10 strut lattice (1.76 M DOF, 1000 cells of 880 nodes) at full size: residual
+    forces and full-rule tangents of 32 seeded cells, the greedy on the full snapshot matrix, and
+    the FP64 and FP32 reduced actions on sampled cells."""
+    case = latgen.make_case("strut10")
+    prob = Problem(case)
+    u0 = ON.predictor(prob, 1, None, None)
+    u = u0 + 0.001 * latgen.uniform_field(prob.n_dof, 17)
+    u[prob.fixed] = u0[prob.fixed]
+    lat = L.Lattice.from_case(case)
+    ud = torch.tensor(u, device="cuda")
+    cells = np.sort(np.random.default_rng(18).choice(prob.lat.n_cells, 32, replace=False)).astype(np.int32)
+    out = lat.assemble_residual_tangent(ud, local_forces=True, tangent=False)
+    ul = prob.local(u)
+    f_ref = OC.internal_force(prob.cell, ul[cells], prob.mu_cells[cells], prob.lam).reshape(32, -1).T
+    assert _rel(out["f"].cpu().numpy()[:, cells], f_ref) < RTOL64
+    ct = torch.tensor(cells, device="cuda")
+    Kf = lat.assemble_residual_tangent(ud, quad=0, cells=ct, residual=False, tangent=True)["K"].cpu()
+    assert _rel(Kf, OC.tangent(prob.cell, ul[cells], prob.mu_cells[cells], prob.lam)) < RTOL64
+    sel = lat.select_principal_cells(ud, 5e-3, 256)
+    assert 1 <= sel["n_r"] <= 256
+    al = sel["alpha"].cpu().numpy()
+    S = sel["S"].cpu().numpy()
+    assert np.abs(al[:, S] - np.eye(len(S))).max() < 1e-9
+    Kp = sel["Kp"].cpu().numpy()
+    assert _rel(Kp[:2], OC.tangent(prob.cell, ul[S[:2]], prob.mu_cells[S[:2]], prob.lam)) < RTOL64
+    X = latgen.uniform_field((lat.sizes.n_loc, lat.sizes.n_cells), 19)
+    Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda")).cpu().numpy()
+    Y_ref = OR.reduced_apply(prob.cell, Kp, al[:, cells], X[:, cells])
+    assert _rel(Y[:, cells], Y_ref) < 1e-10
+    lat.close()
+    # the FP32 action of a mixed-precision handle on the same state
+    lat = L.Lattice.from_case(case, 1)
+    sel32 = lat.select_principal_cells(ud, 5e-3, 256)
+    assert sel32["S"].cpu().numpy().tolist() == S.tolist()
+    Y32 = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=torch.float32)).cpu().numpy()
+    assert _rel(Y32[:, cells], Y_ref) < 2e-6
+    lat.close()

@@ -254,3 +254,28 @@ def test_blocked_coarse_inverse_matches_dense(L):
         outs.append(back[:nd].cpu().numpy())
         lat.close()
     assert np.abs(outs[0] - outs[1]).max() < 1e-10 * np.abs(outs[1]).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_newton_ring32_full_size_oracle_residual(L, precision):
+    """The 32x32 ring lattice (556 034 DOF) at full size, in the configuration the benchmark
+    times: one load step from the predictor with the reduced path (FP64, FP32 or BF16
+    preconditioner).  The oracle's own residual at the GPU solution must meet the Newton
+    tolerance (1e-8) relative to its residual at the predictor (rounding of the two residual
+    evaluations is ~1e-11 of it), and the Dirichlet values must be untouched."""
+    case = latgen.make_case("ring32")
+    prob = Problem(case)
+    lat = L.Lattice.from_case(case, precision)
+    u0 = lat.lattice_predictor(case.top_displacement(1))
+    u = u0.clone()
+    opts = lat.lattice_default_opts(newton_rtol=1e-8)
+    rep = lat.newton_step(u, opts)
+    assert rep.converged and rep.n_r_last >= 1
+    got = u.cpu().numpy()
+    r = prob.residual(got)
+    r0 = prob.residual(u0.cpu().numpy())
+    ratio = np.linalg.norm(r[prob.free]) / np.linalg.norm(r0[prob.free])
+    assert ratio <= 1.01e-8, ratio
+    # Dirichlet values exactly as prescribed
+    assert np.array_equal(got[prob.fixed], u0.cpu().numpy()[prob.fixed])
+    lat.close()
