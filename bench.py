@@ -301,6 +301,7 @@ def run_ours(args):
             raise RuntimeError(f"load path failed at step {k}")
         u_prev2, u_prev = u_prev, u
     u_start = lat_m.lattice_predictor(case.top_displacement(args.state_step + 1), u_prev, u_prev2).clone()
+    u_conv = u_prev.clone() if u_prev is not None else None   # converged state of the last load step
     torch.cuda.synchronize()
 
     def time_newton(lat, opts, steps, warmup, clocks=None, timing=False):
@@ -425,6 +426,19 @@ def run_ours(args):
         out["fp64_full_path"]["kernel_rooflines"] = kernel_rooflines(kt_full, s, None, FP64_PEAK_TFLOPS, hbm_peak)
         lat_b.close()
     # reduced tangent action alone (selection of the benchmark state), L2 flushed between calls
+    if not args.quick and u_conv is not None:
+        # a11: the compliance gradient w.r.t. the per-cell mu scales at the converged state of
+        # the last load step (adjoint through the reduced FETI-DP solve, FP64)
+        lat.adjoint_gradient(u_conv, opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g_adj, J_adj, rep_adj = lat.adjoint_gradient(u_conv, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        out["adjoint"] = {"ms": e0.elapsed_time(e1), "n_theta": int(g_adj.numel()), "J": J_adj,
+                          "krylov_its": rep_adj.krylov_its_total, "defect_corrections": rep_adj.iterations,
+                          "state": "converged load step %d" % args.state_step}
     if args.profile_region == "apply":
         torch.cuda.profiler.start()
     out["apply"] = bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src)
@@ -487,9 +501,14 @@ def bench_kernels_3d(case_name, load_step, hbm_peak, peak_src):
                        % (case_name, s.n_cells, s.n_loc, s.n_dof, load_step)}
     t = _median_ms(lambda: lat.assemble_residual_tangent(u), 10, flush)
     res["residual"] = {"ms": t, "gdofs": s.n_dof / t / 1e6, "qp": s.n_q_full * s.n_cells}
-    t = _median_ms(lambda: lat.assemble_residual_tangent(u, quad=1, residual=False), 10, flush)
-    res["snapshots"] = {"ms": t, "qp": s.n_q_reduced * s.n_cells,
-                        "bytes_written": 8.0 * s.nnz * s.n_cells}
+    K = torch.empty((s.n_cells, s.nnz), dtype=torch.float64, device="cuda")
+    t = _median_ms(lambda: lat.assemble_residual_tangent(u, quad=1, residual=False, K_out=K), 10, flush)
+    res["snapshots"] = {"ms": t, "qp": s.n_q_reduced * s.n_cells, "bytes_written": 8.0 * s.nnz * s.n_cells,
+                        "write_gbs": 8.0 * s.nnz * s.n_cells / t / 1e6}
+    t = _median_ms(lambda: lat.assemble_residual_tangent(u, quad=0, residual=False, K_out=K), 5, flush)
+    res["tangents_full_rule"] = {"ms": t, "qp": s.n_q_full * s.n_cells,
+                                 "note": "every cell at the full rule (the plain path's assembly)"}
+    del K
     sel = lat.select_principal_cells(u, eps, 256)
     t = _median_ms(lambda: lat.select_principal_cells(u, eps, 256), 5, flush)
     res["select"] = {"ms": t, "eps": eps, "n_r": sel["n_r"],
@@ -509,9 +528,38 @@ def bench_kernels_3d(case_name, load_step, hbm_peak, peak_src):
                     "binding": max(byts / (hbm_peak * 1e9), flops / (alu * 1e12)) / t}
         del x, y
     del flush
+    res["sweep_fp32"] = apply_sweep(lat, u, s, torch.float32, 4, FP32_PEAK_TFLOPS, hbm_peak)
     lat.close()
     torch.cuda.empty_cache()
     return res
+
+
+NR_SWEEP = (1, 2, 4, 8, 16, 32, 64)
+
+
+def apply_sweep(lat, u, s, dt, eb, alu_peak, hbm_peak, reps=20):
+    """Reduced action with caller-given principals (the first N_r cells) and coefficients drawn
+    per cell from a flat Dirichlet distribution (rng 8), N_r over NR_SWEEP; L2 flushed before
+    every timed call."""
+    import numpy as np
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    x = torch.rand((s.n_loc, s.n_cells), dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    stacked = s.n_loc * s.n_cells
+    out = []
+    for n_r in NR_SWEEP:
+        S = torch.arange(n_r, dtype=torch.int32)
+        al = torch.tensor(np.random.default_rng(8).dirichlet(np.ones(n_r), size=s.n_cells).T.copy())
+        lat.set_principal_cells(u, S, al)
+        t = _median_ms(lambda: lat.apply_reduced_tangent(x, y), reps, flush) * 1e-3
+        flops = 2.0 * n_r * s.nnz * s.n_cells
+        byts = 2.0 * eb * stacked + eb * n_r * s.n_cells + eb * n_r * s.nnz
+        out.append({"n_r": n_r, "us": t * 1e6, "gdofs": stacked / t / 1e9,
+                    "hbm_frac": byts / t / 1e9 / hbm_peak, "alu_frac": flops / t / 1e12 / alu_peak,
+                    "binding": max(byts / (hbm_peak * 1e9), flops / (alu_peak * 1e12)) / t})
+    del flush, x, y
+    return out
 
 
 def bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src):
@@ -547,6 +595,8 @@ def bench_apply(lat, lat_m, u_start, s, hbm_peak, peak_src):
                                          "frac": flops / t / 1e12 / alu_peak, "flops": flops},
                                  "binding": max(byts / (hbm_peak * 1e9), flops / (alu_peak * 1e12)) / t}}
     del flush
+    res["sweep_fp64"] = apply_sweep(lat, u_start, s, torch.float64, 8, FP64_PEAK_TFLOPS, hbm_peak)
+    res["sweep_fp32"] = apply_sweep(lat_m, u_start, s, torch.float32, 4, FP32_PEAK_TFLOPS, hbm_peak)
     return res
 
 

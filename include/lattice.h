@@ -163,6 +163,18 @@ lat_status select_principal_cells(lat_handle h, const double* u_glob, double eps
                                   int32_t force_all, int32_t* S, int32_t* n_r, double* alpha,
                                   double* K_p);
 
+/* Caller-given principal set for the reduced tangent action (Eq. romstiffnessmatrix with S and
+ * alpha chosen by the caller instead of by Algorithm 1; the paper has no such entry point, its
+ * principal set always comes from the greedy).  u_glob (dev, FP64 [n_dof]): state at which the
+ * principal tangents K^r are evaluated (full rule).  S (dev, int32 [n_r]): principal cell
+ * indices in [0, n_cells).  alpha (dev, FP64 [n_r][n_cells]): coefficients.  All three are
+ * caller-owned and read during the call.  Afterwards apply_reduced_tangent uses this set
+ * (newton_step, lattice_prepare_solver and adjoint_gradient run their own selection).
+ * Errors: LAT_EINVAL (null pointer, n_r outside [1, n_cells], an index out of range),
+ * LAT_ENEG_JACOBIAN (det F <= 0 in a principal cell). */
+lat_status set_principal_cells(lat_handle h, const double* u_glob, const int32_t* S, int32_t n_r,
+                               const double* alpha);
+
 /* Reduced tangent action Y[:, s] = sum_r alpha_r^s K^r X[:, s] (Eq. romstiffnessmatrix) on
  * cell-stacked vectors (dev) [n_loc][n_cells] of type dtype (0 = FP64, 1 = FP32) with the
  * selection held by the handle (FP32 uses FP32 copies of K^r and alpha). */

@@ -200,11 +200,11 @@ __global__ void __launch_bounds__(256)
       const int cc = blockIdx.x * NC + c;
       als[r * NC + c] = cc < A.n_cells ? alpha[(size_t)(r0 + r) * A.n_cells + cc] : T(0);
     }
-    for (int bi = 0; bi < nb; ++bi)
-      for (int t = lane; t < nr * DD; t += 32) {
-        const int r = t / DD, e = t - r * DD;
-        ks[(bi * RCH + r) * DD + e] = Kp[(size_t)(r0 + r) * A.nnz + (size_t)(b0 + bi) * DD + e];
-      }
+    for (int t = lane; t < nb * nr * DD; t += 32) {   // one flat pass: loads in flight together
+      const int bi = t / (nr * DD), rem = t - bi * nr * DD;
+      const int r = rem / DD, e = rem - r * DD;
+      ks[(bi * RCH + r) * DD + e] = Kp[(size_t)(r0 + r) * A.nnz + (size_t)(b0 + bi) * DD + e];
+    }
     __syncthreads();
     if (!active) continue;
     for (int r = 0; r < nr; ++r) {
@@ -256,10 +256,11 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
   } else {
     KernelTimer kt(h, "apply_reduced");
-    if (D == 3 && sizeof(T) == 4 && h->n_r <= 2) {
-      // FP32 with few principals in 3D: the 27 neighbour blocks dominate, and a thread per
-      // (cell, node) with the alpha-combined block formed in registers needs no staging and
-      // keeps more warps in flight (measured faster; in FP64 the staged form is faster)
+    if (D == 3 && sizeof(T) == 4) {
+      // FP32 in 3D: a thread per (cell, node) with the alpha-combined block formed in registers
+      // needs no staging and keeps more warps in flight; the staged form's 81 neighbour values
+      // per thread cost it occupancy (measured 2x slower for N_r = 4 to 64 on the strut
+      // lattice; in FP64 the staged form is the faster one)
       dim3 blk(32, 8);
       dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
       LAT_LAUNCH(h, k_apply_reduced<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, h->n_r, Kp, alpha, X, Y));

@@ -296,6 +296,41 @@ extern "C" lat_status select_principal_cells(lat_handle h, const double* u_glob,
   });
 }
 
+// Caller-given principal set and coefficients (Eq. romstiffnessmatrix with S and alpha chosen by
+// the caller instead of Algorithm 1): principal tangents at the full rule, FP32 copies in the
+// mixed modes.  Used to measure the reduced action at a chosen N_r.
+extern "C" lat_status set_principal_cells(lat_handle h, const double* u_glob, const int32_t* S, int32_t n_r,
+                                          const double* alpha) {
+  if (!h || !u_glob || !S || !alpha) return LAT_EINVAL;
+  return guard(h, [&] {
+    LAT_REQUIRE(n_r >= 1 && n_r <= h->n_cells, LAT_EINVAL, "n_r must be in [1, n_cells]");
+    std::vector<int32_t> hs(n_r);
+    LAT_CUDA(cudaMemcpyAsync(hs.data(), S, n_r * sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    for (int32_t c : hs) LAT_REQUIRE(c >= 0 && c < h->n_cells, LAT_EINVAL, "principal cell index out of range");
+    h->force_all = false;
+    h->n_r = n_r;
+    h->S.ensure(n_r);
+    LAT_CUDA(cudaMemcpyAsync(h->S.p, S, n_r * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->stream));
+    const size_t na = (size_t)n_r * h->n_cells;
+    h->alpha.ensure(na);
+    LAT_CUDA(cudaMemcpyAsync(h->alpha.p, alpha, na * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    bool neg = false;
+    h->Kp.ensure((size_t)n_r * h->nnz);
+    run_tangent(h, u_glob, 0, h->S.p, n_r, h->Kp.p, &neg);
+    LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 in a principal tangent");
+    if (h->prec != LAT_FP64) {
+      const int64_t n = (int64_t)n_r * h->nnz;
+      h->Kp32.ensure(n);
+      LAT_LAUNCH(h, k_to_f32<<<div_up(n, 256), 256, 0, h->stream>>>(n, h->Kp.p, h->Kp32.p));
+      h->alpha32.ensure(na);
+      LAT_LAUNCH(h, k_to_f32<<<div_up((int64_t)na, 256), 256, 0, h->stream>>>((int64_t)na, h->alpha.p, h->alpha32.p));
+      LAT_CHECK_LAUNCH();
+    }
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+  });
+}
+
 // ---------------------------------------------------------------------------------------------
 // Allocation-free variant of greedy_select.
 //

@@ -20,7 +20,8 @@ STATUS = {0: "LAT_OK", 1: "LAT_EINVAL", 2: "LAT_ENOMEM", 3: "LAT_ECUDA", 4: "LAT
           5: "LAT_ENOT_CONVERGED", 6: "LAT_EINDEFINITE", 7: "LAT_ETIMEOUT"}
 EXPORTS = ["lattice_setup", "lattice_destroy", "lattice_sizes", "lattice_last_error",
            "lattice_set_mu_scale", "lattice_predictor", "lattice_gather", "assemble_residual_tangent",
-           "greedy_select", "select_principal_cells", "apply_reduced_tangent", "lattice_default_opts",
+           "greedy_select", "select_principal_cells", "set_principal_cells", "apply_reduced_tangent",
+           "lattice_default_opts",
            "newton_step", "adjoint_gradient", "feti_apply", "lattice_prepare_solver", "feti_to_global",
            "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve",
            "lattice_set_timing", "lattice_kernel_time", "lattice_launch_count", "greedy_select_static"]
@@ -83,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "assemble_residual_tangent": [P, P, I32, P, I32, P, P, P, P],
         "greedy_select": [P, P, I64, I32, D, I32, P, P, P, P, P, P],
         "select_principal_cells": [P, P, D, I32, I32, P, P, P, P],
+        "set_principal_cells": [P, P, P, I32, P],
         "apply_reduced_tangent": [P, P, P, I32],
         "lattice_default_opts": [P, C.POINTER(NewtonOpts)],
         "newton_step": [P, P, I32, C.POINTER(NewtonOpts), C.POINTER(NewtonReport)],
@@ -256,12 +258,16 @@ class Lattice:
         return x
 
     def assemble_residual_tangent(self, u, quad=0, cells=None, residual=True, local_forces=False,
-                                  tangent=False):
+                                  tangent=False, K_out=None):
         s = self.sizes
         n_sel = s.n_cells if cells is None else int(cells.numel())
         r = self.dof_vector() if residual else None
         f = self.cell_vector() if local_forces else None
-        K = torch.zeros((n_sel, s.nnz), dtype=torch.float64, device=self.device) if tangent else None
+        K = K_out
+        if K is None and tangent:
+            K = torch.zeros((n_sel, s.nnz), dtype=torch.float64, device=self.device)
+        if K is not None:
+            assert K.shape == (n_sel, s.nnz) and K.dtype == torch.float64 and K.is_contiguous()
         mdf = C.c_double(0)
         self._check(self._lib.assemble_residual_tangent(self.h, _ptr(u), quad, _ptr(cells), n_sel, _ptr(r),
                                                         _ptr(f), _ptr(K), C.byref(mdf)))
@@ -293,6 +299,14 @@ class Lattice:
                                                      _ptr(S), C.byref(n_r), _ptr(alpha), _ptr(Kp)))
         k = n_r.value
         return dict(S=S[:k], alpha=alpha[:k], Kp=Kp[:k], n_r=k)
+
+    def set_principal_cells(self, u, S, alpha):
+        """Caller-given principal cells S (int32 [n_r]) and coefficients alpha ([n_r, n_cells])
+        for the reduced tangent action; K^r evaluated at u."""
+        S = S.to(device=self.device, dtype=torch.int32).contiguous()
+        alpha = alpha.to(device=self.device, dtype=torch.float64).contiguous()
+        assert alpha.shape == (S.numel(), self.sizes.n_cells)
+        self._check(self._lib.set_principal_cells(self.h, _ptr(u), _ptr(S), int(S.numel()), _ptr(alpha)))
 
     def apply_reduced_tangent(self, x, y=None):
         y = torch.empty_like(x) if y is None else y

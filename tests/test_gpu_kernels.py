@@ -251,3 +251,26 @@ def test_full_size_strut10_sampled(L):
     Y32 = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=torch.float32)).cpu().numpy()
     assert _rel(Y32[:, cells], Y_ref) < 2e-6
     lat.close()
+
+
+@pytest.mark.parametrize("name,n_r", [("ring8", 5), ("strut2", 3)])
+def test_set_principal_cells_apply(L, name, n_r):
+    """Caller-given principal cells and Dirichlet-distributed coefficients: the reduced action
+    equals the oracle's sum_r alpha_r^s K^r x_s (FP64 exactly to rounding, FP32 to 2e-6)."""
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    u = _state(case, 0.02, 21)
+    S = np.arange(n_r, dtype=np.int32)
+    al = np.random.default_rng(8).dirichlet(np.ones(n_r), size=prob.lat.n_cells).T.copy()
+    Kp = OC.tangent(prob.cell, prob.local(u)[S], prob.mu_cells[S], prob.lam)
+    X = latgen.uniform_field((prob.cell.n_nodes * prob.cell.d, prob.lat.n_cells), 22)
+    Y_ref = OR.reduced_apply(prob.cell, Kp, al, X)
+    for prec, dt, tol in ((0, torch.float64, 1e-10), (1, torch.float32, 2e-6)):
+        lat = L.Lattice.from_case(case, prec)
+        lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor(S), torch.tensor(al))
+        Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=dt)).cpu().numpy()
+        assert _rel(Y, Y_ref) < tol
+        with pytest.raises(L.LatticeError):
+            lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor([prob.lat.n_cells]),
+                                    torch.ones((1, prob.lat.n_cells)))
+        lat.close()
