@@ -247,6 +247,78 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// FP32 form with 16-byte accesses (used in 3D): a warp owns local node a, each lane 4 consecutive
+// cells.
+// Per principal r: z = sum_b K^r_ab x_b over the node's neighbour blocks (block values
+// warp-uniform, loaded as float4 from blocks padded to a multiple of 4 values; x_b as float4 over
+// the lane's 4 cells, L1 resident after the first principal), then y += alpha_r (x) z.  About 85 %
+// of the issued instructions are multiply-adds.  Needs n_cells % 4 == 0 (16-byte aligned rows).
+template <int D>
+__global__ void __launch_bounds__(256)
+    k_apply_v4(int n_cells, int nn, const int* __restrict__ blk_ptr, const int* __restrict__ blk_col, int64_t nblk,
+               int n_r, const float* __restrict__ Kb, const float* __restrict__ alpha, const float* __restrict__ X,
+               float* __restrict__ Y) {
+  constexpr int DDP = D == 2 ? 4 : 12;   // padded block length
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int a = blockIdx.y * 8 + warp;
+  const int c0 = (blockIdx.x * 32 + lane) * 4;
+  if (a >= nn || c0 >= n_cells) return;
+  const int b0 = blk_ptr[a], b1 = blk_ptr[a + 1];
+  float4 y[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) y[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int r = 0; r < n_r; ++r) {
+    float4 z[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float* kr = Kb + (size_t)r * nblk * DDP;
+    for (int bi = b0; bi < b1; ++bi) {
+      const int b = blk_col[bi];
+      float4 x[D];
+#pragma unroll
+      for (int j = 0; j < D; ++j) x[j] = __ldg(reinterpret_cast<const float4*>(X + (size_t)(b * D + j) * n_cells + c0));
+      float k[DDP];
+#pragma unroll
+      for (int q = 0; q < DDP / 4; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(kr + (size_t)bi * DDP) + q);
+        k[4 * q] = v.x;
+        k[4 * q + 1] = v.y;
+        k[4 * q + 2] = v.z;
+        k[4 * q + 3] = v.w;
+      }
+#pragma unroll
+      for (int i = 0; i < D; ++i)
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const float kv = k[i * D + j];
+          z[i].x = fmaf(kv, x[j].x, z[i].x);
+          z[i].y = fmaf(kv, x[j].y, z[i].y);
+          z[i].z = fmaf(kv, x[j].z, z[i].z);
+          z[i].w = fmaf(kv, x[j].w, z[i].w);
+        }
+    }
+    const float4 al = __ldg(reinterpret_cast<const float4*>(alpha + (size_t)r * n_cells + c0));
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      y[i].x = fmaf(al.x, z[i].x, y[i].x);
+      y[i].y = fmaf(al.y, z[i].y, y[i].y);
+      y[i].z = fmaf(al.z, z[i].z, y[i].z);
+      y[i].w = fmaf(al.w, z[i].w, y[i].w);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) *reinterpret_cast<float4*>(Y + (size_t)(a * D + i) * n_cells + c0) = y[i];
+}
+
+// principal blocks [n_r][nblk][9] -> [n_r][nblk][12] (zero padded) for 16-byte loads in 3D
+__global__ void k_pad12(int64_t n_blocks, const float* __restrict__ K, float* __restrict__ Kb) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= n_blocks * 12) return;
+  const int64_t blk = t / 12;
+  const int e = (int)(t % 12);
+  Kb[t] = e < 9 ? K[blk * 9 + e] : 0.f;
+}
+
 template <typename T, int D, bool FETI>
 void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T* X, T* Y) {
   if (h->force_all) {
@@ -254,6 +326,26 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
     dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
+  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0) {
+    // 3D FP32 (measured 2.5x faster than the per-(cell, node) form on the strut lattice; in 2D
+    // the staged form is faster: its 9 neighbour blocks stay in registers across principals)
+    const int64_t nblk = h->nnz / (D * D);
+    const float* Kb = reinterpret_cast<const float*>(Kp);
+    if (D == 3) {
+      if (h->kp12_version != h->sel_version) {
+        const int64_t nb = (int64_t)h->n_r * nblk;
+        h->Kp12.ensure((size_t)nb * 12);
+        LAT_LAUNCH(h, k_pad12<<<div_up(nb * 12, 256), 256, 0, h->stream>>>(nb, h->Kp32.p, h->Kp12.p));
+        h->kp12_version = h->sel_version;
+      }
+      Kb = h->Kp12.p;
+    }
+    dim3 grid(div_up(h->n_cells, 128), div_up(h->n_nodes_cell, 8));
+    KernelTimer kt(h, "apply_reduced");
+    LAT_LAUNCH(h, k_apply_v4<D><<<grid, 256, 0, h->stream>>>(h->n_cells, h->n_nodes_cell, h->blk_ptr.p, h->blk_col.p,
+                                                              nblk, h->n_r, Kb, reinterpret_cast<const float*>(alpha),
+                                                              reinterpret_cast<const float*>(X),
+                                                              reinterpret_cast<float*>(Y)));
   } else {
     KernelTimer kt(h, "apply_reduced");
     if (D == 3 && sizeof(T) == 4) {

@@ -143,6 +143,8 @@ struct lat_ctx {
   DBuf<float> alpha32;
   DBuf<double> Kp;                    // [n_r][nnz]
   DBuf<float> Kp32;
+  DBuf<float> Kp12;                     // 3D FP32 principal blocks padded to 12 values
+  int64_t sel_version = 0, kp12_version = -1;   // principal-set changes / the padded copy's
   // greedy workspaces
   DBuf<double> g_delta, g_Z, g_beta, g_inf, g_nrm2, g_norms, g_part, g_maxres;
   DBuf<int> g_state;                  // [0] done, [1] n_r, [2] s_next

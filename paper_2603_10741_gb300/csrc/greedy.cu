@@ -275,6 +275,7 @@ void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool
     LAT_LAUNCH(h, k_to_f32<<<div_up(n, 256), 256, 0, h->stream>>>(n, h->Kp.p, h->Kp32.p));
     LAT_CHECK_LAUNCH();
   }
+  ++h->sel_version;
 }
 
 extern "C" lat_status select_principal_cells(lat_handle h, const double* u_glob, double eps,
@@ -327,6 +328,7 @@ extern "C" lat_status set_principal_cells(lat_handle h, const double* u_glob, co
       LAT_LAUNCH(h, k_to_f32<<<div_up((int64_t)na, 256), 256, 0, h->stream>>>((int64_t)na, h->alpha.p, h->alpha32.p));
       LAT_CHECK_LAUNCH();
     }
+    ++h->sel_version;
     LAT_CUDA(cudaStreamSynchronize(h->stream));
   });
 }

@@ -595,7 +595,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->cell_class);
   rel(h->coarse_ptr); rel(h->coarse_src); rel(h->cb_dest); rel(h->cb_perm); rel(h->cb_A);
   rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->coarse_row); rel(h->coarse_col);
-  rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32);
+  rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32); rel(h->Kp12);
   rel(h->g_delta); rel(h->g_Z); rel(h->g_beta); rel(h->g_inf); rel(h->g_nrm2); rel(h->g_norms);
   rel(h->g_part); rel(h->g_maxres); rel(h->g_state); rel(h->g_scale);
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
