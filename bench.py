@@ -215,7 +215,7 @@ def run_reference(args):
 KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
            "local_segmm", "local_gemv", "local_tc", "gj_update", "gj_pivot", "densify", "phi_schur",
            "coarse_blocked", "coarse_gemv", "local_segmm_dual", "local_gemv_dual", "local_tc_dual",
-           "local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in", "krylov_orth"]
+           "local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in", "dual_schur", "krylov_orth"]
 
 
 def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
@@ -225,6 +225,7 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
         2 (n_R + n_P) n_R flops per cell (dense local inverse and coarse restriction);
     *_dual: the same on the dual block inside the interface solve, 2 (n_D + n_P) n_D per cell;
     *_dual_in: all rows, dual columns (input supported on the dual DOFs), 2 (n_R + n_P) n_D;
+    dual_schur: the Dirichlet interface preconditioner's local products, 2 n_D^2 per cell;
     apply_reduced: 2 N_r nnz flops per cell (Eq. romstiffnessmatrix);
     apply_percell: the plain path, 8 nnz bytes of K^s and the two vectors per cell;
     coarse_gemv: the explicit coarse inverse streamed once: FP64 (2 n_primal^2 flops, FP64-ALU
@@ -240,6 +241,8 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
         return 2.0 * (n_d + n_p) * n_d * n_s, "flops"
     if name in ("local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in"):
         return 2.0 * (n_rr + n_p) * n_d * n_s, "flops"
+    if name == "dual_schur":
+        return 2.0 * n_d * n_d * n_s, "flops"
     if name == "apply_reduced" and n_r:
         return 2.0 * n_r * nnz * n_s, "flops"
     if name == "apply_percell":
@@ -263,7 +266,7 @@ def kernel_rooflines(kt, s, n_r, alu_peak, hbm_peak, tensor_peak=None, mixed=Fal
             tc = name.startswith("local_tc")
             # the local products run in the mode's precision; the Krylov operator and the FP64
             # coarse product in FP64
-            peak = tensor_peak if tc else (alu_peak if name.startswith("local_") else FP64_PEAK_TFLOPS)
+            peak = tensor_peak if tc else (alu_peak if name.startswith(("local_", "dual_")) else FP64_PEAK_TFLOPS)
             ach = work / avg_s / 1e12
             rows.append({"kernel": name, "bound": "tensor" if tc else "alu", "achieved": ach, "peak": peak,
                          "unit": "TFLOP/s", "frac": ach / peak, "total_ms": k["total_ms"],

@@ -599,7 +599,8 @@ __global__ void __launch_bounds__(256)
 // FP32 operands accumulate in FP32 (TG = float), FP64 in FP64 (BN a multiple of 16).
 template <typename TG, int BN>
 __global__ void __launch_bounds__(256)
-    k_local_segmm(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, const TG* __restrict__ G,
+    k_local_segmm(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, int scale_mul,
+                  const TG* __restrict__ G,
                   const int* __restrict__ tile_seg,
                   const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                   const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ rc,
@@ -656,7 +657,7 @@ __global__ void __launch_bounds__(256)
   for (int v = 0; v < NV; ++v) {
     const int s = cells[tx + 16 * v];
     if (s < 0) continue;
-    const double inv = 1.0 / cscale[s];
+    const double inv = scale_mul ? cscale[s] : 1.0 / cscale[s];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int gi = i0 + ty + 16 * u;
@@ -670,7 +671,8 @@ __global__ void __launch_bounds__(256)
 // is the bound (two FP64 multiply-adds per clock per SM), so shared-memory traffic is free and a
 // narrow tile only trims the multiply-adds spent on the padding of short key segments.
 __global__ void __launch_bounds__(256)
-    k_local_segmm_n4(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, const double* __restrict__ G,
+    k_local_segmm_n4(int n_cells, int n_Kr, int n_Kc, int n_P, int ldg, int64_t kstride, int scale_mul,
+                     const double* __restrict__ G,
                      const int* __restrict__ tile_seg,
                      const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                      const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ rc,
@@ -712,7 +714,8 @@ __global__ void __launch_bounds__(256)
   const int s = cells[tx];
   const int gi = i0 + ty;
   if (s >= 0 && gi < rows)
-    Y[out_row(gi, n_Kr, rr, pdofs) * n_cells + s] = gi < n_Kr ? acc * (1.0 / cscale[s]) : acc;
+    Y[out_row(gi, n_Kr, rr, pdofs) * n_cells + s] =
+        gi < n_Kr ? acc * (scale_mul ? cscale[s] : 1.0 / cscale[s]) : acc;
 }
 
 // Dirichlet interface preconditioner, local part: y_D = c_s S_DD^{slot(s)} x_D on the dual rows
@@ -1174,10 +1177,10 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
     KernelTimer kt(h, tg_segmm[mode]);
     dim3 grid(h->max_tiles, div_up(nKr + nP, 64));
     if (lo)
-      LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride,
+      LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, 0,
           h->G32.p + off, h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     else
-      LAT_LAUNCH(h, k_local_segmm_n4<<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G.p + off,
+      LAT_LAUNCH(h, k_local_segmm_n4<<<grid, 256, 0, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, 0, h->G.p + off,
           h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
   }
   LAT_CHECK_LAUNCH();
@@ -1216,10 +1219,23 @@ void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2
                                                           h->dual_l2.p, h->dual_scale.p, r, 1.0, t1));
   LAT_CHECK_LAUNCH();
   if (h->iface == 0) {
-    // Dirichlet: local dual Schur complements of the cells' principals
+    // Dirichlet: local dual Schur complements of the cells' principals, c_s S_DD^{slot(s)} x_D;
+    // with few keys as a segmented product over the key-ordered cells (as the local inverses)
     const int nD = h->n_R - h->n_I;
     const size_t shm = (size_t)nD * sizeof(double);
-    if (h->prec == LAT_FP64) {
+    const bool seg = (int64_t)h->n_keys * 8 <= h->n_cells;
+    if (seg) {
+      KernelTimer kt(h, "dual_schur");
+      const int* rd = h->rdofs.p + h->n_I;
+      dim3 grid(h->max_tiles, div_up(nD, 64));
+      if (h->prec == LAT_FP64)
+        LAT_LAUNCH(h, k_local_segmm_n4<<<grid, 256, 0, h->stream>>>(h->n_cells, nD, nD, 0, nD, (int64_t)nD * nD, 1,
+            h->SDD.p, h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rd, rd, h->pdofs.p, t1, t2));
+      else
+        LAT_LAUNCH(h, k_local_segmm<float, 64><<<grid, 256, 0, h->stream>>>(h->n_cells, nD, nD, 0, nD,
+            (int64_t)nD * nD, 1, h->SDD32.p, h->tile_seg.p, h->tile_c0.p, h->seg_ptr.p, h->perm.p, h->c_cell.p, rd,
+            rd, h->pdofs.p, t1, t2));
+    } else if (h->prec == LAT_FP64) {
       LAT_CUDA(cudaFuncSetAttribute(k_dual_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
       LAT_LAUNCH(h, k_dual_schur<double><<<h->n_cells, 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD.p,
           h->key_slot.p, h->c_cell.p, h->rdofs.p, t1, t2));
