@@ -254,6 +254,15 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
     return None, None
 
 
+# DRAM bytes per launch from one ncu capture of the FP64 headline iteration (dram__bytes_read.sum
+# + dram__bytes_write.sum), with the summary that holds the command; None once a kernel changes
+MEASURED_TRAFFIC_FP64 = {
+    "coarse_gemv": (305.54e6, "profiles/k_gemv_xs_fp64_ring32.md"),
+    "local_segmm": (105.84e6, "profiles/k_local_segmm_n4_fp64_ring32.md"),
+    "apply_reduced": (7.95e6, "profiles/k_apply_staged_fp64_ring32.md"),
+}
+
+
 def kernel_rooflines(kt, s, n_r, alu_peak, hbm_peak, tensor_peak=None, mixed=False):
     """Roofline entry for every timed kernel that has a work model, largest total time first."""
     rows = []
@@ -386,7 +395,10 @@ def run_ours(args):
                           mixed=args.precision != "fp64")
     if rl:
         top = dict(rl[0])
-        top["traffic"] = None
+        tr = MEASURED_TRAFFIC_FP64.get(top["kernel"]) if args.precision == "fp64" and args.case == "ring32" else None
+        top["traffic"] = tr[0] if tr else None
+        if tr:
+            top["traffic_source"] = tr[1]
         top["peak_source"] = ({"fp64": "FP64 ALU, recipe table (1.20 measured)",
                                "fp32": "FP32 ALU, 152 SM x 128 lanes x 2 x 2.07 GHz"}.get(args.precision, peak_src)
                               if top["bound"] == "alu" else peak_src)
