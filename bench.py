@@ -544,9 +544,46 @@ def bench_kernels_3d(case_name, load_step, hbm_peak, peak_src):
         del x, y
     del flush
     res["sweep_fp32"] = apply_sweep(lat, u, s, torch.float32, 4, FP32_PEAK_TFLOPS, hbm_peak)
+    res["local_product"] = local_product_3d(case, lat, u, eps)
     lat.close()
     torch.cuda.empty_cache()
     return res
+
+
+def local_product_3d(case, lat32, u, eps):
+    """a9's principal-block x cell-multivector product on the 3D blocks (n_R ~ 2616): one
+    application of K^-rom (the whole [G; Phi^T] of each key) in FP64, FP32 and on the tensor
+    cores (BF16 pairs), timed by the library's kernel timers.  Corner-only primal set (no
+    enrichment): only the product is measured here, not a solve."""
+    import torch
+    from paper_2603_10741_gb300 import LAT_FP64, LAT_MIXED_BF16, LAT_MIXED_FP32, Lattice
+    _, bf16_peak, _ = peaks()
+    out = {}
+    for tag, prec, kname, peak in (("fp32", LAT_MIXED_FP32, "local_segmm", FP32_PEAK_TFLOPS),
+                                   ("bf16", LAT_MIXED_BF16, "local_tc", bf16_peak),
+                                   ("fp64", LAT_FP64, "local_segmm", FP64_PEAK_TFLOPS)):
+        L = lat32 if prec == LAT_MIXED_FP32 else Lattice.from_case(case, prec)
+        o = L.lattice_default_opts(max_enrich=0)
+        L.select_principal_cells(u, eps, 256)
+        L.lattice_prepare_solver(u, o)
+        s = L.sizes
+        v = L.krylov_vector()
+        v.uniform_(-1.0, 1.0)
+        L.feti_apply(1, v)
+        torch.cuda.synchronize()
+        L.lattice_set_timing(True)
+        for _ in range(5):
+            L.feti_apply(1, v)
+        t, n = L.lattice_kernel_time(kname)
+        L.lattice_set_timing(False)
+        work = 2.0 * (s.n_r_local + s.n_p_local) * s.n_r_local * s.n_cells
+        sec = t / n * 1e-3
+        out[tag] = {"kernel": kname, "us": sec * 1e6, "flops": work, "tflops": work / sec / 1e12,
+                    "frac": work / sec / 1e12 / peak, "peak": peak, "n_r_local": s.n_r_local}
+        if L is not lat32:
+            L.close()
+        torch.cuda.empty_cache()
+    return out
 
 
 NR_SWEEP = (1, 2, 4, 8, 16, 32, 64)
