@@ -193,7 +193,8 @@ def test_checkpoint_roundtrip(L, tmp_path):
 @pytest.mark.parametrize("name", ["ring8"])
 def test_bf16_tensor_core_local_product(L, name):
     """BF16 mode: the tcgen05 principal-block product inside K^-rom agrees with the FP64 one to
-    BF16 accuracy (8-bit mantissa operands, FP32 accumulation over ~570 terms)."""
+    the accuracy of its BF16 operand pairs (~16-bit mantissas; the dropped low x low product is
+    ~2^-16 relative) with FP32 accumulation over ~570 terms."""
     case = latgen.make_case(name)
     prob = Problem(case)
     ud = torch.tensor(_u0(prob, 1, 0.0005, 4), device="cuda")
@@ -210,7 +211,7 @@ def test_bf16_tensor_core_local_product(L, name):
         lat.close()
     ref, got = outs
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-    assert err < 2e-2, err
+    assert err < 1e-4, err
 
 
 def test_newton_bf16_mode_ring4(L):
