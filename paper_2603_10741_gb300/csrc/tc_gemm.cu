@@ -1,47 +1,51 @@
 // Principal-block x cell-multivector product on the 5th-generation tensor cores (tcgen05) for the
 // BF16 mixed mode: the local part of K^-rom (Eq. ifetidp_precond, Section 3.3.1) for all cells,
 //   Y[rows of cell s] = [G; Phi^T]_{key(s)} X_R^s,   G = (K_RR^r)^{-1} of the cell's principal,
-// as a segmented GEMM over cells grouped by key: one CTA computes a 128-row x 64-cell tile of
-// one key with A = rows of the key's augmented matrix and B = the 64 cells' remaining values,
-// accumulating in FP32 in tensor memory.  Each operand is a BF16 pair (high part and the BF16
-// rounding of the remainder) and three products G_hi X_hi + G_hi X_lo + G_lo X_hi accumulate
-// into the same tile: ~16-bit operands, which the preconditioner needs on the ill-conditioned
-// local problems of the corner-only primal set (one BF16 rounding stalls FGMRES near 1e-4
-// there).  The epilogue reads the accumulator with tcgen05.ld and applies the per-cell scale
-// 1/c_s on the G rows.
+// as a segmented GEMM over cells grouped by key: one CTA computes MW tiles of 128 rows x TN
+// cells of one key (TN = 64, MW = 1 in use) with A = rows of the key's augmented matrix and
+// B = the cells' remaining values, accumulating
+// in FP32 in tensor memory.  Each operand is a BF16 pair (high part and the BF16 rounding of the
+// remainder) and three products G_hi X_hi + G_hi X_lo + G_lo X_hi accumulate into the same
+// tile: ~16-bit operands, which the preconditioner needs on the ill-conditioned local problems
+// of the corner-only primal set (one BF16 rounding stalls FGMRES near 1e-4 there).  The
+// epilogue reads the accumulators with tcgen05.ld and applies the per-cell scale 1/c_s on the G
+// rows.
 //
 // Operand staging.  Both operands are stored in global memory already tiled in the layout the
 // tensor core reads from shared memory: the canonical no-swizzle K-major layout (8-row x 16-byte
 // core matrices; K-adjacent core matrices 128 B apart, 8-row groups 1024 B apart), one
-// contiguous 16 KiB block per (key, 128-row tile, 64-wide K panel) for A and one 8 KiB block
-// per (cell tile, K panel) for B.  A K panel is then two bulk copies (cp.async.bulk, completing
-// on an mbarrier with its byte count); four stages are in flight.  One elected thread issues the
-// copies and the MMAs (M = 128, N = 64, K = 16 per instruction), commits each stage's MMAs to
-// that stage's "empty" barrier before refilling it, and a final commit releases the epilogue.
-// Every wait is bounded: on a timeout the kernel flags an error, gives outstanding work a
-// bounded chance to finish, frees its tensor memory and returns.
+// contiguous 16 KiB block per (key, 128-row tile, 64-wide K panel) for A and one block per
+// (cell tile, K panel) for B.  A K panel is then MW + 1 bulk copies (cp.async.bulk, completing
+// on an mbarrier with their byte count).  One elected thread issues
+// the copies and the MMAs (M = 128, N = TN, K = 16 per instruction), commits each stage's MMAs
+// to that stage's "empty" barrier before refilling it, and a final commit releases the
+// epilogue.  Three stages are in flight for MW = 1 (four for MW = 2).  Every wait is bounded: on a timeout the kernel flags an error, gives outstanding
+// work a bounded chance to finish, frees its tensor memory and returns.
 #include "common.cuh"
 
 namespace {
 
-constexpr int TM = 128;   // rows of the tile (tensor-memory lanes)
-constexpr int TN = 64;    // cells of the tile (accumulator columns)
+constexpr int TM = 128;   // rows of an M tile (tensor-memory lanes)
 constexpr int TK = 64;    // K panel
 constexpr int KSTEP = 16; // K per tcgen05.mma, kind::f16
-constexpr int STAGES = 4;
-constexpr int TMEM_COLS = 64;          // one FP32 accumulator column per cell of the tile
-constexpr int A_ELEMS = TM * TK;       // 8192 bf16 = 16 KiB
-constexpr int B_ELEMS = TN * TK;       // 4096 bf16 = 8 KiB
+constexpr int A_ELEMS = TM * TK;       // 8192 bf16 = 16 KiB per M tile and K panel
 constexpr int A_BYTES = A_ELEMS * 2;
-constexpr int B_BYTES = B_ELEMS * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES;   // 96 KiB: two CTAs per SM
 constexpr uint32_t LBO = 128;              // K-adjacent core matrices
 constexpr uint32_t SBO = (TK / 8) * 128;   // 8-row groups
 
-// instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                           ((uint32_t)(TM >> 4) << 24);
+// per-configuration sizes: TN cells per tile, MW M tiles of 128 rows per CTA
+template <int TN, int MW>
+struct TcCfg {
+  static constexpr int B_ELEMS = TN * TK;
+  static constexpr int B_BYTES = B_ELEMS * 2;
+  static constexpr int STAGE_BYTES = MW * A_BYTES + B_BYTES;
+  static constexpr int STAGES = MW == 1 ? 3 : 4;   // 72 KiB (three CTAs per SM) or 192 KiB
+  static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES;
+  static constexpr int TMEM_COLS = MW * TN;   // MW accumulators of TN FP32 columns
+  // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                    ((uint32_t)(TM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -82,16 +86,14 @@ __device__ __forceinline__ void mbar_init(uint32_t addr) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(1) : "memory");
 }
 
-// one stage: arm the barrier with the stage's byte count, then the two bulk copies
-__device__ __forceinline__ void load_stage(uint32_t sA, uint32_t sB, uint32_t bar, const void* gA, const void* gB) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)STAGE_BYTES)
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
                : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sA),
-               "l"(gA), "r"((uint32_t)A_BYTES), "r"(bar)
-               : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(sB),
-               "l"(gB), "r"((uint32_t)B_BYTES), "r"(bar)
-               : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -99,42 +101,54 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-// Tensor-core tile: rows [128 mt, 128 mt + 128) of the key's view of [G; Phi^T] times the 64
-// cells of tile `tile` (key-ordered positions [c0, c0 + 64)).  GT: tiled high parts
-// [key][mt][kp][8192] (low parts lo_off elements later), XT: tiled cell vectors
-// [tile][2 KP][4096] (high panels 0..KP-1, low panels KP..2KP-1).  Panel p of the 3 KP panels
-// is (pass, kp) = (p / KP, p % KP): passes G_hi X_hi, G_hi X_lo, G_lo X_hi.
+// Tensor-core tile: rows [128 mt, 128 (mt + MW)) of the key's view of [G; Phi^T] (MW M tiles,
+// the last CTA of a key may have one) times the TN cells of tile `tile` (key-ordered positions
+// [c0, c0 + TN)).  GT: tiled high parts [key][mt][kp][8192] (low parts lo_off elements later),
+// XT: tiled cell vectors [tile][2 KP][TN x 64] (high panels 0..KP-1, low panels KP..2KP-1).
+// Panel p of the 3 KP panels is (pass, kp) = (p / KP, p % KP): passes G_hi X_hi, G_hi X_lo,
+// G_lo X_hi.  With MW = 2 every B panel feeds two M tiles (two accumulators in tensor memory).
+template <int TN, int MW>
 __global__ void __launch_bounds__(128)
     k_local_tc(int n_cells, int n_Kr, int n_P, int MT, int KP, int64_t lo_off, const __nv_bfloat16* __restrict__ GT,
                const __nv_bfloat16* __restrict__ XT, const int* __restrict__ tile_seg,
                const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ pdofs,
                double* __restrict__ Y, int* __restrict__ err) {
+  using C = TcCfg<TN, MW>;
+  constexpr int STAGES = C::STAGES;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x, mt = blockIdx.y;
+  const int tile = blockIdx.x, mt0 = blockIdx.y * MW;
+  const int nm = min(MW, MT - mt0);          // M tiles of this CTA
   const int key = tile_seg[tile];
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[key + 1];
   const int rows = n_Kr + n_P;
   const int P2 = 3 * KP;
+  const uint32_t stage_tx = (uint32_t)(nm * A_BYTES + C::B_BYTES);
   const uint32_t s0 = smem_u32(smem);
-  auto sA = [&](int st) { return s0 + (uint32_t)(st * STAGE_BYTES); };
-  auto sB = [&](int st) { return s0 + (uint32_t)(st * STAGE_BYTES + A_BYTES); };
-  auto gA = [&](int p) {
+  auto sA = [&](int st, int m) { return s0 + (uint32_t)(st * C::STAGE_BYTES + m * A_BYTES); };
+  auto sB = [&](int st) { return s0 + (uint32_t)(st * C::STAGE_BYTES + MW * A_BYTES); };
+  auto gA = [&](int p, int m) {
     const int pass = p / KP, kp = p - pass * KP;
-    return (const void*)(GT + (((size_t)key * MT + mt) * KP + kp) * A_ELEMS + (pass == 2 ? lo_off : 0));
+    return (const void*)(GT + (((size_t)key * MT + mt0 + m) * KP + kp) * A_ELEMS + (pass == 2 ? lo_off : 0));
   };
   auto gB = [&](int p) {
     const int pass = p / KP, kp = p - pass * KP;
-    return (const void*)(XT + ((size_t)tile * 2 * KP + (pass == 1 ? KP + kp : kp)) * B_ELEMS);
+    return (const void*)(XT + ((size_t)tile * 2 * KP + (pass == 1 ? KP + kp : kp)) * C::B_ELEMS);
+  };
+  auto load = [&](int p, int st) {
+    const uint32_t bar = smem_u32(&full[st]);
+    expect_tx(bar, stage_tx);
+    for (int m = 0; m < nm; ++m) bulk_copy(sA(st, m), gA(p, m), (uint32_t)A_BYTES, bar);
+    bulk_copy(sB(st), gB(p), (uint32_t)C::B_BYTES, bar);
   };
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(C::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -155,8 +169,7 @@ __global__ void __launch_bounds__(128)
   if (tid == 0) {
     // producer and MMA issuer in one thread: copies run up to STAGES panels ahead
     int issued = 0;
-    for (; issued < STAGES && issued < P2; ++issued)
-      load_stage(sA(issued), sB(issued), smem_u32(&full[issued]), gA(issued), gB(issued));
+    for (; issued < STAGES && issued < P2; ++issued) load(issued, issued);
     bool ok = true;
     for (int p = 0; p < P2; ++p) {
       const int st = p % STAGES;
@@ -166,17 +179,19 @@ __global__ void __launch_bounds__(128)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int m = 0; m < nm; ++m) {
 #pragma unroll
-      for (int ks = 0; ks < TK / KSTEP; ++ks) {
-        const uint64_t ad = make_desc(sA(st) + ks * 2 * 128);
-        const uint64_t bd = make_desc(sB(st) + ks * 2 * 128);
-        const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
-        asm volatile(
-            "{\n\t.reg .pred q;\n\t"
-            "setp.ne.b32 q, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-            : "memory");
+        for (int ks = 0; ks < TK / KSTEP; ++ks) {
+          const uint64_t ad = make_desc(sA(st, m) + ks * 2 * 128);
+          const uint64_t bd = make_desc(sB(st) + ks * 2 * 128);
+          const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred q;\n\t"
+              "setp.ne.b32 q, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem + (uint32_t)(m * TN)),
+              "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
+              : "memory");
+        }
       }
       mma_commit(smem_u32(&empty[st]));
       if (issued < P2) {
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(128)
           ok = false;
           break;
         }
-        load_stage(sA(st), sB(st), smem_u32(&full[st]), gA(issued), gB(issued));
+        load(issued, st);
         ++issued;
       }
     }
@@ -197,36 +212,38 @@ __global__ void __launch_bounds__(128)
     }
     mma_commit(smem_u32(&done));   // arrives when every MMA issued above has completed
   }
-  // everyone: accumulator complete (bounded wait)
+  // everyone: accumulators complete (bounded wait)
   const bool fin = mbar_wait(smem_u32(&done), 0);
   __syncthreads();
   const bool ok = fin && !fail;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (__syncthreads_and(ok ? 1 : 0)) {
     // epilogue: warp w reads accumulator lanes 32w..32w+31 (tile rows), 16 columns at a time
-    const int gi = mt * TM + warp * 32 + lane;
-    const bool row_ok = gi < rows;
-    const size_t orow = row_ok ? (size_t)(gi < n_Kr ? rr[gi] : pdofs[gi - n_Kr]) : 0;
+    for (int m = 0; m < nm; ++m) {
+      const int gi = (mt0 + m) * TM + warp * 32 + lane;
+      const bool row_ok = gi < rows;
+      const size_t orow = row_ok ? (size_t)(gi < n_Kr ? rr[gi] : pdofs[gi - n_Kr]) : 0;
 #pragma unroll
-    for (int cb = 0; cb < TN; cb += 16) {
-      uint32_t r[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-          "%14, %15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row_ok) {
+      for (int cb = 0; cb < TN; cb += 16) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * TN + cb);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row_ok) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int pos = c0 + cb + j;
-          if (pos >= c_end) continue;
-          const int s = perm[pos];
-          const double v = (double)__uint_as_float(r[j]);
-          Y[orow * n_cells + s] = gi < n_Kr ? v / cscale[s] : v;
+          for (int j = 0; j < 16; ++j) {
+            const int pos = c0 + cb + j;
+            if (pos >= c_end) continue;
+            const int s = perm[pos];
+            const double v = (double)__uint_as_float(r[j]);
+            Y[orow * n_cells + s] = gi < n_Kr ? v / cscale[s] : v;
+          }
         }
       }
     }
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
   }
 }
 
@@ -245,10 +262,12 @@ __global__ void __launch_bounds__(128)
 // kx = kp (high part) or KP + kp (low part), cell c = position c0 + c of the tile's key segment
 // (zero past the segment's end), column kp * 64 + k of the view (zero beyond n_K).  One CTA per
 // (tile, kp); gathered 8-byte reads, 16-byte writes.
+template <int TN>
 __global__ void k_pack_xt(int n_cells, int n_K, int KP, const double* __restrict__ X, const int* __restrict__ tile_seg,
                           const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                           const int* __restrict__ rc, __nv_bfloat16* __restrict__ XT) {
-  __shared__ __align__(16) __nv_bfloat16 hi[B_ELEMS], lo[B_ELEMS];
+  constexpr int BE = TN * TK;
+  __shared__ __align__(16) __nv_bfloat16 hi[BE], lo[BE];
   const int tile = blockIdx.x, kp = blockIdx.y;
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[tile_seg[tile] + 1];
@@ -262,9 +281,9 @@ __global__ void k_pack_xt(int n_cells, int n_K, int KP, const double* __restrict
     lo[core_off(c, k)] = __float2bfloat16(v - __bfloat162float(h));
   }
   __syncthreads();
-  uint4* dh = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + kp) * B_ELEMS);
-  uint4* dl = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + KP + kp) * B_ELEMS);
-  for (int t = threadIdx.x; t < B_ELEMS / 8; t += blockDim.x) {
+  uint4* dh = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + kp) * BE);
+  uint4* dl = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + KP + kp) * BE);
+  for (int t = threadIdx.x; t < BE / 8; t += blockDim.x) {
     dh[t] = reinterpret_cast<const uint4*>(hi)[t];
     dl[t] = reinterpret_cast<const uint4*>(lo)[t];
   }
@@ -318,9 +337,11 @@ void run_g_to_bf16(lat_ctx* h, size_t n) {
   LAT_CHECK_LAUNCH();
 }
 
-// Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores.  The tile
-// list groups cells of one key in runs of 64 (seg_bn = 64 in the mixed modes).
-void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
+namespace {
+
+template <int TN, int MW>
+void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int* tseg, const int* tc0, int n_tiles) {
+  using C = TcCfg<TN, MW>;
   const int lo_r = mode == KINV_DUAL ? h->n_I : 0, lo_c = mode == KINV_FULL ? 0 : h->n_I;
   const int nKr = h->n_R - lo_r, nKc = h->n_R - lo_c;
   const int MT = div_up(nKr + h->n_P, TM);
@@ -328,17 +349,26 @@ void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
   const int* rr = h->rdofs.p + lo_r;
   const int* rc = h->rdofs.p + lo_c;
   const int KPmax = std::max(1, div_up(h->n_R, TK));
-  h->Xb16.ensure((size_t)h->max_tiles * 2 * KPmax * B_ELEMS);
-  LAT_LAUNCH(h, k_pack_xt<<<dim3(h->max_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nKc, KP, X, h->tile_seg.p,
-                                                                         h->tile_c0.p, h->seg_ptr.p, h->perm.p, rc,
-                                                                         h->Xb16.p));
-  LAT_CUDA(cudaFuncSetAttribute(k_local_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-  dim3 grid(h->max_tiles, MT);
+  h->Xb16.ensure((size_t)n_tiles * 2 * KPmax * C::B_ELEMS);
+  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(n_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nKc, KP, X, tseg, tc0,
+                                                                         h->seg_ptr.p, h->perm.p, rc, h->Xb16.p));
+  LAT_CUDA(cudaFuncSetAttribute(k_local_tc<TN, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM_BYTES));
+  dim3 grid(n_tiles, div_up(MT, MW));
   static const char* const tg[3] = {"local_tc", "local_tc_dual", "local_tc_dual_in"};
   KernelTimer kt(h, tg[mode]);
-  LAT_LAUNCH(h, k_local_tc<<<grid, 128, SMEM_BYTES, h->stream>>>(h->n_cells, nKr, h->n_P, MT, KP, h->g16_lo[mode],
-                                                                  h->G16[mode].p, h->Xb16.p, h->tile_seg.p,
-                                                                  h->tile_c0.p, h->seg_ptr.p, h->perm.p,
-                                                                  h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p));
+  LAT_LAUNCH(h, (k_local_tc<TN, MW><<<grid, 128, C::SMEM_BYTES, h->stream>>>(
+                    h->n_cells, nKr, h->n_P, MT, KP, h->g16_lo[mode], h->G16[mode].p, h->Xb16.p, tseg, tc0,
+                    h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p)));
   LAT_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+// Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores, on the
+// 64-cell tiles of the mixed modes' segmented products, three CTAs per SM.  (128-cell tiles with
+// two M tiles per CTA halve the operand traffic per multiply-add but leave SMs idle at the
+// problem sizes here: 99 CTAs for the 10x10x10 strut lattice, measured slower.)
+void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
+  launch_tc<64, 1>(h, X, Y, mode, h->tile_seg.p, h->tile_c0.p, h->max_tiles);
 }

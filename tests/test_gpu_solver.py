@@ -280,3 +280,28 @@ def test_newton_ring32_full_size_oracle_residual(L, precision):
     # Dirichlet values exactly as prescribed
     assert np.array_equal(got[prob.fixed], u0.cpu().numpy()[prob.fixed])
     lat.close()
+
+
+def test_bf16_tensor_core_long_segments(L):
+    """BF16 mode with few keys (at most three principals: eps 5e-2) on the 32x32 ring lattice, so
+    that the key segments hold >= 96 cells on average (many full 64-cell tiles per key, as on
+    the 3D lattices); the tensor-core product must agree with the FP64 one to the accuracy of
+    the BF16 pairs."""
+    case = latgen.make_case("ring32")
+    prob = Problem(case)
+    ud = torch.tensor(_u0(prob, 1, 0.0005, 4), device="cuda")
+    outs = []
+    for prec in (0, 2):
+        lat = L.Lattice.from_case(case, prec)
+        opts = lat.lattice_default_opts(eps=5e-2, max_enrich=0)
+        sel = lat.select_principal_cells(ud, 5e-2, 256)
+        assert 1 <= sel["n_r"] <= 3, sel["n_r"]
+        lat.lattice_prepare_solver(ud, opts)
+        s = lat.sizes
+        rng = np.random.default_rng(6)
+        v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
+        outs.append(lat.feti_apply(1, v)[: s.n_loc * s.n_cells + s.n_primal].cpu().numpy())
+        lat.close()
+    ref, got = outs
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 1e-4, err
