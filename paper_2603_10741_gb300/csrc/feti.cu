@@ -248,17 +248,9 @@ __global__ void k_from_global(int64_t n_nodes, int D, int nn, int n_cells, int n
   }
 }
 
-// rhs local part: -f on free remaining rows, 0 on corner and fixed rows
-__global__ void k_neg_masked(int64_t n, const double* __restrict__ f, const uint8_t* __restrict__ fixed,
-                             double* __restrict__ out) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = fixed[i] ? 0.0 : -f[i];
-}
-
 // ---------------------------------------------------------------------------------------------
 // preconditioner setup kernels
 // ---------------------------------------------------------------------------------------------
-// per cell: principal with the largest coefficient, scale c_s = sum_r alpha_r^s, key
 // per cell: the principal whose normalised snapshot is nearest (largest cosine), and the
 // least-squares scale c_s of K^s ~ c_s K^{r(s)} in the snapshot inner product.  The cosines come
 // from the greedy's coordinates: <t^s, t^{s_r}> / (|t^s| |t^{s_r}|) = sum_i beta_i^s beta_i^{s_r}
@@ -1098,7 +1090,6 @@ const double* la_of(lat_ctx* h, const double* v) { return v + (size_t)h->n_loc *
 
 // w_u = K~ v_u (+ B^T v_l when with_bt), w_l = B v_u  (saddle-point operator)
 void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda) {
-  const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
   const double* vP = pr_of(h, v);
   // the Krylov operator stays FP64 in every mode: FGMRES then solves the FP64 system to its
   // tolerance, while the mixed modes lower the precision of the preconditioner only
