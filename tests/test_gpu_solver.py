@@ -305,3 +305,33 @@ def test_bf16_tensor_core_long_segments(L):
     ref, got = outs
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < 1e-4, err
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_error_against_oracle_by_precision(L, precision, capsys):
+    """The errors of the displacements (4x4 ring lattice, three load steps) and of the adjoint
+    gradient (2x2 ring lattice, end state) against the FP64 oracle, in each precision mode: FP64
+    within 1e-10 (relative L2), the mixed modes within the Newton tolerance 1e-8; the gradient's
+    defect correction uses the exact FP64 tangent action in every mode, so it stays within 1e-9
+    of the oracle's.  The errors are printed for the record."""
+    from paper_2603_10741_gb300 import solve_load_path
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, _ = ON.load_path(prob, n_steps=3, tol=1e-13)
+    lat = L.Lattice.from_case(case, precision)
+    rtol = 1e-12 if precision == 0 else 1e-10
+    u, _ = solve_load_path(lat, case, lat.lattice_default_opts(newton_rtol=rtol), steps=3)
+    err_u = np.linalg.norm(u.cpu().numpy() - ref[-1]) / np.linalg.norm(ref[-1])
+    lat.close()
+    case2 = latgen.make_case("ring2")
+    prob2 = Problem(case2)
+    states, _ = ON.load_path(prob2, tol=1e-13)
+    g_ref = OA.gradient(prob2, states[-1])
+    lat = L.Lattice.from_case(case2, precision)
+    g, J, rep = lat.adjoint_gradient(torch.tensor(states[-1], device="cuda"), lat.lattice_default_opts(eps=1e-4))
+    err_g = np.abs(g.cpu().numpy() - g_ref).max() / np.abs(g_ref).max()
+    lat.close()
+    with capsys.disabled():
+        print(f"\n[precision {precision}] displacement rel L2 error {err_u:.2e}, gradient max rel error {err_g:.2e}")
+    assert err_u < (1e-10 if precision == 0 else 1e-8), err_u
+    assert err_g < 1e-9, err_g
