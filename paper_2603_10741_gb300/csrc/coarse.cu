@@ -154,11 +154,10 @@ void bgemm(lat_ctx* h, int m, std::vector<const double*> a, std::vector<const do
       P.b[z] = b[z0 + z];
       P.c[z] = c[z0 + z];
     }
-    const int64_t tiles64 = (int64_t)nz * div_up(m, 64) * div_up(m, 64);
-    const int64_t tiles32 = (int64_t)nz * div_up(m, 32) * div_up(m, 32);
-    if (tiles64 >= 2 * h->n_sm)
+    const int T = fp64_tile(m, nz, h->n_sm);
+    if (T == 64)
       LAT_LAUNCH(h, (k_bgemm<TA, TB, 64><<<dim3(div_up(m, 64), div_up(m, 64), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));
-    else if (tiles32 >= h->n_sm)
+    else if (T == 32)
       LAT_LAUNCH(h, (k_bgemm<TA, TB, 32><<<dim3(div_up(m, 32), div_up(m, 32), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));
     else
       LAT_LAUNCH(h, (k_bgemm<TA, TB, 16><<<dim3(div_up(m, 16), div_up(m, 16), nz), 256, 0, h->stream>>>(m, P, alpha, beta)));

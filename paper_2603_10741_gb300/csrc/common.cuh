@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <map>
@@ -348,6 +349,24 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
                 double* max_res_host);
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti);
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
+// square tile (64, 32 or 16) for batched FP64 products over n x n matrices: the least padded
+// work per busy SM (padding of n to the tile, and the share of the SMs the tiles occupy)
+inline int fp64_tile(int n, int64_t batch, int n_sm) {
+  int best = 64;
+  double best_cost = 1e300;
+  for (int T : {64, 32, 16}) {
+    const int64_t per = (n + T - 1) / T;
+    const double waste = (double)(per * T) * (per * T) / ((double)n * n);
+    const double busy = std::min(1.0, (double)(batch * per * per) / n_sm);
+    const double cost = waste / busy;
+    if (cost < best_cost * 0.9) {   // prefer the larger tile unless clearly better
+      best_cost = cost;
+      best = T;
+    }
+  }
+  return best;
+}
+
 inline void drop_pcg_graph(lat_ctx* h) {
   if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
   h->pcg_exec = nullptr;

@@ -927,12 +927,11 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
     }
     {
       KernelTimer kt(h, "gj_update");
-      const int64_t tiles64 = (int64_t)batch * div_up(n, 64) * div_up(n, 64);
-      const int64_t tiles32 = (int64_t)batch * div_up(n, 32) * div_up(n, 32);
-      if (tiles64 >= 2 * h->n_sm)
+      const int T = fp64_tile(n, batch, h->n_sm);
+      if (T == 64)
         LAT_LAUNCH(h, k_gj_update<64><<<dim3(div_up(n, 64), div_up(n, 64), batch), 256, 0, h->stream>>>(
                           n, bs, k0, kw, A, Pinv.p, Cbuf.p, Rbuf.p));
-      else if (tiles32 >= h->n_sm)
+      else if (T == 32)
         LAT_LAUNCH(h, k_gj_update<32><<<dim3(div_up(n, 32), div_up(n, 32), batch), 256, 0, h->stream>>>(
                           n, bs, k0, kw, A, Pinv.p, Cbuf.p, Rbuf.p));
       else
