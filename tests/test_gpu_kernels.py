@@ -274,3 +274,29 @@ def test_set_principal_cells_apply(L, name, n_r):
             lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor([prob.lat.n_cells]),
                                     torch.ones((1, prob.lat.n_cells)))
         lat.close()
+
+
+@pytest.mark.parametrize("dims", [(3, 1, 1), (2, 2, 1), (1, 1, 5)])
+def test_apply_ragged_3d_cell_counts(L, dims):
+    """3D strut lattices with 3, 4 and 5 cells: the FP32 action takes the 16-byte four-cell path
+    only when the cell count is a multiple of four and the per-(cell, node) path otherwise; both
+    must equal the oracle's sum_r alpha_r^s K^r x_s (caller-given principals and coefficients)."""
+    Xr, E = latgen.strut_cell(6, 0.2)
+    lat_geo = latgen.tile(Xr, E, dims)
+    n = lat_geo.n_cells
+    case = latgen.LoadCase(name="strut-ragged", lattice=lat_geo, mu=1.0, lam=4.0,
+                           mu_scale=latgen.mu_scale(n, 9), total_strain=0.05, n_steps=5, eps=5e-3)
+    prob = Problem(case)
+    u = _state(case, 0.01, 23)
+    n_r = min(2, n)
+    S = np.arange(n_r, dtype=np.int32)
+    al = latgen.dirichlet_coefficients(n_r, n, 8)
+    Kp = OC.tangent(prob.cell, prob.local(u)[S], prob.mu_cells[S], prob.lam)
+    X = latgen.uniform_field((prob.cell.n_nodes * 3, n), 24)
+    Y_ref = OR.reduced_apply(prob.cell, Kp, al, X)
+    for prec, dt, tol in ((0, torch.float64, 1e-10), (1, torch.float32, 2e-6)):
+        lat = L.Lattice.from_case(case, prec)
+        lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor(S), torch.tensor(al))
+        Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=dt)).cpu().numpy()
+        assert _rel(Y, Y_ref) < tol
+        lat.close()
