@@ -41,15 +41,20 @@ typedef enum {
   LAT_ECUDA = 3,           /* CUDA runtime error */
   LAT_ENEG_JACOBIAN = 4,   /* some quadrature point has det F <= 0 */
   LAT_ENOT_CONVERGED = 5,  /* Newton, Armijo or Krylov iteration cap reached */
-  LAT_EINDEFINITE = 6,     /* a local remaining-DOF matrix or the coarse matrix is not definite */
-  LAT_ETIMEOUT = 7         /* reserved: a bounded device-side wait gave up */
+  LAT_EINDEFINITE = 6,     /* a local remaining-DOF matrix or the coarse matrix is singular (a zero
+                              or non-finite pivot; negative pivots are tolerated and trigger the
+                              primal enrichment) */
+  LAT_ETIMEOUT = 7         /* a bounded device-side wait (tensor-core pipeline) gave up */
 } lat_status;
 
 typedef enum {
   LAT_FP64 = 0,        /* everything FP64 */
-  LAT_MIXED_FP32 = 1,  /* residual, Newton update, Krylov vectors, coarse problem FP64;
-                          reduced tangent action and local preconditioner blocks FP32 */
-  LAT_MIXED_BF16 = 2   /* as FP32, with the local preconditioner blocks in BF16 (FP32 accumulate) */
+  LAT_MIXED_FP32 = 1,  /* residual, Newton update, Krylov vectors and operator (the reduced tangent
+                          action inside FGMRES), coarse factorisation FP64; preconditioner
+                          (local inverses, dual Schur complements, coarse application) FP32;
+                          apply_reduced_tangent also accepts FP32 vectors */
+  LAT_MIXED_BF16 = 2   /* as FP32, with the local inverse products on the tensor cores: operands as
+                          BF16 high/low pairs, FP32 accumulation */
 } lat_precision;
 
 /* Lattice description: one reference cell of Q1 elements, repeated by unit translations
