@@ -335,3 +335,25 @@ def test_error_against_oracle_by_precision(L, precision, capsys):
         print(f"\n[precision {precision}] displacement rel L2 error {err_u:.2e}, gradient max rel error {err_g:.2e}")
     assert err_u < (1e-10 if precision == 0 else 1e-8), err_u
     assert err_g < 1e-9, err_g
+
+
+def test_bf16_tensor_core_3d_blocks(L):
+    """The 10x10x10 strut lattice (n_R 2616: 41 K panels per pass, 21 row tiles; three keys of
+    ~100-800 cells): the tensor-core product on the 3D blocks must agree with the FP64 product
+    to the accuracy of the BF16 pairs."""
+    case = latgen.make_case("strut10")
+    outs = []
+    for prec in (0, 2):
+        lat = L.Lattice.from_case(case, prec)
+        u = lat.lattice_predictor(case.top_displacement(1))
+        opts = lat.lattice_default_opts(max_enrich=0)
+        lat.select_principal_cells(u, opts.eps, 256)
+        lat.lattice_prepare_solver(u, opts)
+        s = lat.sizes
+        rng = np.random.default_rng(7)
+        v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
+        outs.append(lat.feti_apply(1, v)[: s.n_loc * s.n_cells + s.n_primal].cpu().numpy())
+        lat.close()
+    ref, got = outs
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < 1e-4, err
