@@ -39,27 +39,8 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
     y[i] = a * x[i] + b * y[i];
 }
 
-// PCG step lengths with a breakdown guard: sc[0] rz, sc[1] pq, sc[2] rz_new, sc[3] alpha,
-// sc[4] beta, sc[5] frozen (once p.q <= 0 or r.z <= 0 the iteration stops updating)
-__global__ void k_pcg_alpha(double* sc) {
-  const bool ok = sc[5] == 0.0 && sc[1] > 0.0 && sc[0] > 0.0;
-  if (!ok) sc[5] = 1.0;
-  sc[3] = ok ? sc[0] / sc[1] : 0.0;
-}
-__global__ void k_pcg_beta(double* sc) {
-  const bool ok = sc[5] == 0.0 && sc[2] > 0.0 && sc[0] > 0.0;
-  if (!ok) sc[5] = 1.0;
-  sc[4] = ok ? sc[2] / sc[0] : 0.0;
-  sc[0] = sc[2];
-}
-// y += sgn * a[0] * x
-__global__ void k_axpy_s(int64_t n, const double* __restrict__ a, double sgn, const double* __restrict__ x,
-                         double* __restrict__ y) {
-  const double c = sgn * a[0];
-  if (c == 0.0) return;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] += c * x[i];
-}
+// PCG scalars (see k_sum_part_pcg): sc[0] rz, sc[1] pq, sc[2] rz_new, sc[3] alpha, sc[4] beta,
+// sc[5] frozen (once p.q <= 0 or r.z <= 0 the iteration stops updating)
 // p = z + b[0] p  (p left unchanged when the iteration is frozen)
 __global__ void k_xpby_s(int64_t n, const double* __restrict__ z, const double* __restrict__ b,
                          const double* __restrict__ frozen, double* __restrict__ p) {
@@ -85,6 +66,41 @@ __global__ void k_sum_part(int n, const double* __restrict__ part, double* __res
   for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
   v = block_sum(v, red);
   if (threadIdx.x == 0) out[0] = v;
+}
+
+// the same sum into the PCG scalars, followed by the step length (step = 0: sc[1] = p.q,
+// alpha = rz / pq) or the direction coefficient (step = 1: sc[2] = r.z, beta = rz_new / rz),
+// with the breakdown guard that freezes the iteration: one launch per PCG dot and scalar
+__global__ void k_sum_part_pcg(int n, const double* __restrict__ part, double* __restrict__ sc, int step) {
+  __shared__ double red[32];
+  double v = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += part[i];
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    if (step == 0) {
+      sc[1] = v;
+      const bool ok = sc[5] == 0.0 && sc[1] > 0.0 && sc[0] > 0.0;
+      if (!ok) sc[5] = 1.0;
+      sc[3] = ok ? sc[0] / sc[1] : 0.0;
+    } else {
+      sc[2] = v;
+      const bool ok = sc[5] == 0.0 && sc[2] > 0.0 && sc[0] > 0.0;
+      if (!ok) sc[5] = 1.0;
+      sc[4] = ok ? sc[2] / sc[0] : 0.0;
+      sc[0] = sc[2];
+    }
+  }
+}
+
+// x += a[0] p and r -= a[0] q in one pass (the PCG updates of solution and residual)
+__global__ void k_axpy2_s(int64_t n, const double* __restrict__ a, const double* __restrict__ p,
+                          const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+  const double c = a[0];
+  if (c == 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += c * p[i];
+    r[i] -= c * q[i];
+  }
 }
 
 // partial dots of w against the first m vectors of V (stride n): part[i][block]
@@ -738,10 +754,15 @@ __global__ void __launch_bounds__(256)
 // Y_R^s += Phi^{slot(s)} xP(corners of s)
 __global__ void k_phi_n(int n_cells, int n_K, int n_P, int64_t kstride, const double* __restrict__ Phi,
                         const int* __restrict__ slot, const int* __restrict__ rdofs, const int* __restrict__ pidx,
-                        const double* __restrict__ xP, const uint8_t* __restrict__ fixed, double* __restrict__ Y) {
+                        const double* __restrict__ xP, const uint8_t* __restrict__ fixed,
+                        const int* __restrict__ pdofs, double* __restrict__ Y) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
-  if (s >= n_cells || i >= n_K) return;
+  if (s >= n_cells) return;
+  if (i >= n_K) {   // rows n_K.. of the grid clear the corner rows (their values went to g_P)
+    Y[(size_t)pdofs[i - n_K] * n_cells + s] = 0.0;
+    return;
+  }
   const double* ph = Phi + (size_t)slot[s] * kstride + (size_t)i * n_P;
   double v = 0;
   for (int j = 0; j < n_P; ++j) {
@@ -1181,11 +1202,13 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
         h->p_copy.p, wl, h->gP.p, 1));
     run_coarse_solve(h, h->gP.p, pr_of(h, w));
   }
-  LAT_LAUNCH(h, k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl));
   if (h->n_primal) {
-    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nKr), 128, 0, h->stream>>>(ns, nKr, nP, (int64_t)nR * nP,
-        h->Phi.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->pidx.p, pr_of(h, w), h->loc_fixed.p, wl));
+    // w_R += Phi x_P on the view's rows; the extra nP grid rows clear the corner rows
+    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nKr + nP), 128, 0, h->stream>>>(ns, nKr, nP, (int64_t)nR * nP,
+        h->Phi.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->pidx.p, pr_of(h, w), h->loc_fixed.p, h->pdofs.p, wl));
     LAT_CHECK_LAUNCH();
+  } else {
+    LAT_LAUNCH(h, k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl));
   }
 }
 
@@ -1286,7 +1309,7 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
   LAT_CHECK_LAUNCH();
   // PCG on S x = y from x = 0
   LAT_CUDA(cudaMemsetAsync(x, 0, L * sizeof(double), h->stream));
-  double* sc = h->red_part.p + 3000;  // see k_pcg_alpha
+  double* sc = h->red_part.p + 3000;  // PCG scalars, see k_sum_part_pcg
   if (pcg_iters > 0) {
     // PCG until the preconditioned residual r^T M r has dropped by pcg_rtol^2 (checked on the
     // host after every iteration), at most pcg_iters iterations, or until breakdown.  One
@@ -1308,13 +1331,13 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
     auto body = [&]() {
       LAT_LAUNCH(h, k_xpby_s<<<nb, 256, 0, h->stream>>>(L, z, sc + 4, sc + 5, p));
       dual_op(h, p, q, t1, t2);
-      dev_dot(h, L, p, q, sc + 1);
-      LAT_LAUNCH(h, k_pcg_alpha<<<1, 1, 0, h->stream>>>(sc));
-      LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, 1.0, p, x));
-      LAT_LAUNCH(h, k_axpy_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, -1.0, q, y));
+      const int rb = red_blocks(L);
+      LAT_LAUNCH(h, k_dot_part<<<rb, 256, 0, h->stream>>>(L, p, q, h->red_part.p + 1024));
+      LAT_LAUNCH(h, k_sum_part_pcg<<<1, 512, 0, h->stream>>>(rb, h->red_part.p + 1024, sc, 0));   // alpha
+      LAT_LAUNCH(h, k_axpy2_s<<<nb, 256, 0, h->stream>>>(L, sc + 3, p, q, x, y));
       dual_precond(h, y, z, t1, t2, wloc);
-      dev_dot(h, L, y, z, sc + 2);
-      LAT_LAUNCH(h, k_pcg_beta<<<1, 1, 0, h->stream>>>(sc));
+      LAT_LAUNCH(h, k_dot_part<<<rb, 256, 0, h->stream>>>(L, y, z, h->red_part.p + 1024));
+      LAT_LAUNCH(h, k_sum_part_pcg<<<1, 512, 0, h->stream>>>(rb, h->red_part.p + 1024, sc, 1));   // beta
       if (check)
         LAT_CUDA(cudaMemcpyAsync(h->h_pinned + 8, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LAT_CHECK_LAUNCH();
