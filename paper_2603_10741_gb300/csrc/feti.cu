@@ -148,10 +148,11 @@ __global__ void k_scale_dev(int64_t n, const double* __restrict__ x, const doubl
 // ---------------------------------------------------------------------------------------------
 // yP[p] = (accumulate ? yP[p] : 0) + sum over the copies of p of loc[entry]
 __global__ void k_primal_assemble(int64_t n_primal, const int* __restrict__ pptr, const int* __restrict__ pc,
-                                  const double* __restrict__ loc, double* __restrict__ yP, int accumulate) {
+                                  const double* __restrict__ loc, double* __restrict__ yP, int accumulate,
+                                  const double* __restrict__ base = nullptr) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n_primal) return;
-  double v = accumulate ? yP[p] : 0.0;
+  double v = base ? base[p] : (accumulate ? yP[p] : 0.0);   // yP = base + sum when base is given
   for (int c = pptr[p]; c < pptr[p + 1]; ++c) v += loc[pc[c]];
   yP[p] = v;
 }
@@ -1197,9 +1198,8 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
   LAT_CHECK_LAUNCH();
   if (h->n_primal) {
     // g_P = v_P + sum_s A_P^T Phi^T v_R   (from the corner rows of wl)
-    LAT_CUDA(cudaMemcpyAsync(h->gP.p, pr_of(h, v), h->n_primal * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     LAT_LAUNCH(h, k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
-        h->p_copy.p, wl, h->gP.p, 1));
+        h->p_copy.p, wl, h->gP.p, 1, pr_of(h, v)));
     run_coarse_solve(h, h->gP.p, pr_of(h, w));
   }
   if (h->n_primal) {
