@@ -63,8 +63,9 @@ __global__ void __launch_bounds__(256) k_bgemm(int m, BatchPtrs P, double alpha,
       Bs[r][c] = v;
     }
     __syncthreads();
+    const int lim = min(32, m - k0);   // no multiply-adds on the zero padding of the last chunk
 #pragma unroll 8
-    for (int l = 0; l < 32; ++l) {
+    for (int l = 0; l < lim; ++l) {
       double av[U], bv[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) av[u] = As[ty + 16 * u][l];

@@ -649,8 +649,9 @@ __global__ void __launch_bounds__(256)
       Xs[r][c] = (gl < n_Kc && s >= 0) ? (TG)X[(size_t)rc[gl] * n_cells + s] : TG(0);
     }
     __syncthreads();
+    const int lim = min(32, n_Kc - l0);   // no multiply-adds on the padding of the last chunk
 #pragma unroll 8
-    for (int l = 0; l < 32; ++l) {
+    for (int l = 0; l < lim; ++l) {
       TG gv[4], xv[NV];
 #pragma unroll
       for (int u = 0; u < 4; ++u) gv[u] = Gs[ty + 16 * u][l];
@@ -717,8 +718,9 @@ __global__ void __launch_bounds__(256)
       Xs[r][c] = (gl < n_Kc && s >= 0) ? X[(size_t)rc[gl] * n_cells + s] : 0.0;
     }
     __syncthreads();
+    const int lim = min(32, n_Kc - l0);   // no multiply-adds on the padding of the last chunk
 #pragma unroll 8
-    for (int l = 0; l < 32; ++l) acc = fma(Gs[ty][l], Xs[l][tx], acc);
+    for (int l = 0; l < lim; ++l) acc = fma(Gs[ty][l], Xs[l][tx], acc);
   }
   const int s = cells[tx];
   const int gi = i0 + ty;
