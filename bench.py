@@ -460,6 +460,7 @@ def run_ours(args):
     if not args.quick and rank == 0:
         # the 3D configuration's per-cell rows (a1-a7) at full size
         out["strut10_kernels"] = bench_kernels_3d("strut10", 1, hbm_peak, peak_src)
+        out["strut20_apply"] = bench_apply_3d("strut20", 1, hbm_peak, peak_src)
     if args.profile_region == "apply":
         torch.cuda.profiler.stop()
     # end to end through host buffers: H2D of the state, one Newton iteration, D2H of the result
@@ -587,6 +588,33 @@ def local_product_3d(case, lat32, u, eps):
 
 
 NR_SWEEP = (1, 2, 4, 8, 16, 32, 64)
+
+
+def bench_apply_3d(case_name, load_step, hbm_peak, peak_src):
+    """Row a7 on the largest 3D lattice (20^3 strut cells: 8000 cells x 2640 local DOF): the FP32
+    reduced action against N_r, beside a device copy of the same bytes from X to Y (the stream
+    rate this traffic pattern reaches); L2 flushed before every timed call."""
+    import torch
+    import latgen
+    from paper_2603_10741_gb300 import LAT_MIXED_FP32, Lattice
+    case = latgen.make_case(case_name)
+    lat = Lattice.from_case(case, LAT_MIXED_FP32)
+    s = lat.sizes
+    u = lat.lattice_predictor(case.top_displacement(load_step))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    x = torch.rand((s.n_loc, s.n_cells), dtype=torch.float32, device="cuda")
+    y = torch.empty_like(x)
+    t = _median_ms(lambda: y.copy_(x), 20, flush) * 1e-3
+    copy = {"us": t * 1e6, "bytes": 8.0 * x.numel(), "gbs": 8.0 * x.numel() / t / 1e9,
+            "frac": 8.0 * x.numel() / t / 1e9 / hbm_peak, "peak_source": peak_src}
+    del x, y, flush
+    res = {"workload": "%s: %d cells, %d local DOF each, %d DOF, affine predictor of load step %d"
+                       % (case_name, s.n_cells, s.n_loc, s.n_dof, load_step),
+           "copy_x_to_y": copy,
+           "sweep_fp32": apply_sweep(lat, u, s, torch.float32, 4, FP32_PEAK_TFLOPS, hbm_peak)}
+    lat.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def apply_sweep(lat, u, s, dt, eb, alu_peak, hbm_peak, reps=20):

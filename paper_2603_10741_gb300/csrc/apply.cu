@@ -143,8 +143,15 @@ __host__ __device__ constexpr int stage_rch() {
   return D == 2 ? (sizeof(T) == 4 ? 32 : 16) : (sizeof(T) == 4 ? 8 : 4);
 }
 
+// The FP32 action in 2D: four CTAs per SM (64 registers) measured 1.4x faster than the three
+// that an unconstrained choice of 72 registers allows
 template <typename T, int D, bool FETI>
-__global__ void __launch_bounds__(256)
+__host__ __device__ constexpr int stage_min_blocks() {
+  return D == 2 && sizeof(T) == 4 && !FETI ? 4 : 1;
+}
+
+template <typename T, int D, bool FETI>
+__global__ void __launch_bounds__(256, stage_min_blocks<T, D, FETI>())
     k_apply_staged(ApplyArgs A, int n_r, const T* __restrict__ Kp, const T* __restrict__ alpha,
                    const T* __restrict__ X, T* __restrict__ Y) {
   constexpr int MAXNB = StageCfg<D>::MAXNB, CPT = StageCfg<D>::CPT, RCH = stage_rch<T, D>();
@@ -247,76 +254,131 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// FP32 form with 16-byte accesses (used in 3D): a warp owns local node a, each lane 4 consecutive
-// cells.
-// Per principal r: z = sum_b K^r_ab x_b over the node's neighbour blocks (block values
-// warp-uniform, loaded as float4 from blocks padded to a multiple of 4 values; x_b as float4 over
-// the lane's 4 cells, L1 resident after the first principal), then y += alpha_r (x) z.  About 85 %
-// of the issued instructions are multiply-adds.  Needs n_cells % 4 == 0 (16-byte aligned rows).
-template <int D>
-__global__ void __launch_bounds__(256)
-    k_apply_v4(int n_cells, int nn, const int* __restrict__ blk_ptr, const int* __restrict__ blk_col, int64_t nblk,
-               int n_r, const float* __restrict__ Kb, const float* __restrict__ alpha, const float* __restrict__ X,
-               float* __restrict__ Y) {
-  constexpr int DDP = D == 2 ? 4 : 12;   // padded block length
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int a = blockIdx.y * 8 + warp;
-  const int c0 = (blockIdx.x * 32 + lane) * 4;
-  if (a >= nn || c0 >= n_cells) return;
-  const int b0 = blk_ptr[a], b1 = blk_ptr[a + 1];
-  float4 y[D];
-#pragma unroll
-  for (int i = 0; i < D; ++i) y[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int r = 0; r < n_r; ++r) {
-    float4 z[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float* kr = Kb + (size_t)r * nblk * DDP;
-    for (int bi = b0; bi < b1; ++bi) {
-      const int b = blk_col[bi];
-      float4 x[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) x[j] = __ldg(reinterpret_cast<const float4*>(X + (size_t)(b * D + j) * n_cells + c0));
-      float k[DDP];
-#pragma unroll
-      for (int q = 0; q < DDP / 4; ++q) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(kr + (size_t)bi * DDP) + q);
-        k[4 * q] = v.x;
-        k[4 * q + 1] = v.y;
-        k[4 * q + 2] = v.z;
-        k[4 * q + 3] = v.w;
-      }
-#pragma unroll
-      for (int i = 0; i < D; ++i)
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          const float kv = k[i * D + j];
-          z[i].x = fmaf(kv, x[j].x, z[i].x);
-          z[i].y = fmaf(kv, x[j].y, z[i].y);
-          z[i].z = fmaf(kv, x[j].z, z[i].z);
-          z[i].w = fmaf(kv, x[j].w, z[i].w);
-        }
-    }
-    const float4 al = __ldg(reinterpret_cast<const float4*>(alpha + (size_t)r * n_cells + c0));
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-      y[i].x = fmaf(al.x, z[i].x, y[i].x);
-      y[i].y = fmaf(al.y, z[i].y, y[i].y);
-      y[i].z = fmaf(al.z, z[i].z, y[i].z);
-      y[i].w = fmaf(al.w, z[i].w, y[i].w);
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < D; ++i) *reinterpret_cast<float4*>(Y + (size_t)(a * D + i) * n_cells + c0) = y[i];
+// FP32 form in 3D: node groups staged in shared memory.  A CTA owns one group of GR nodes of the
+// cell (chosen at setup so that their neighbourhoods overlap) and 128 consecutive cells.  It
+// copies, with cp.async and all copies in flight at once, the x rows of the union of the group's
+// neighbour nodes for its 128 cells (3 rows of 512 B per union node) and the group's principal
+// blocks (a chunk of principals at a time) into shared memory; then warp w forms node w's three
+// outputs for its lane's 4 cells: per principal z = sum_b K^r_ab x_b (block values broadcast,
+// x_b as one 16-byte shared load per DOF, the union position of b broadcast by shuffle), and
+// y += alpha_r (x) z.  No load of the inner loop waits on L2.  PAIR uses packed FP32x2
+// multiply-adds over cell pairs.  Needs n_cells % 4 == 0 (16-byte aligned rows).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// principal blocks [n_r][nblk][9] -> [n_r][nblk][12] (zero padded) for 16-byte loads in 3D
-__global__ void k_pad12(int64_t n_blocks, const float* __restrict__ K, float* __restrict__ Kb) {
+template <int GR, bool PAIR>
+__global__ void __launch_bounds__(GR * 32)
+    k_apply_groups(int n_cells, const int* __restrict__ grp_rows, const int* __restrict__ grp_ucptr,
+                   const int* __restrict__ grp_ucol, const int* __restrict__ grp_pp, const int* __restrict__ pair_u,
+                   int64_t n_pairs, int n_r, int rch, const float* __restrict__ Kg, const float* __restrict__ alpha,
+                   const float* __restrict__ X, float* __restrict__ Y) {
+  extern __shared__ __align__(16) float smf[];
+  const int g = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile0 = blockIdx.x * 128;
+  const int nct = min(128, n_cells - tile0);                 // a multiple of 4
+  const int u0 = grp_ucptr[g], nu = grp_ucptr[g + 1] - u0;
+  const int gp0 = grp_pp[g * (GR + 1)], np = grp_pp[g * (GR + 1) + GR] - gp0;
+  float* xs = smf;                                           // [nu * 3][128]
+  float* ks = smf + (size_t)nu * 3 * 128;                    // [rch][np][12]
+  for (int t = warp; t < nu * 3; t += GR) {
+    const int b = grp_ucol[u0 + t / 3], j = t % 3;
+    float* dst = xs + (size_t)t * 128 + lane * 4;
+    if (lane * 4 < nct) cp_async16(dst, X + (size_t)(b * 3 + j) * n_cells + tile0 + lane * 4);
+    else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const int a = grp_rows[g * GR + warp];
+  const int q0 = grp_pp[g * (GR + 1) + warp] - gp0, nq = grp_pp[g * (GR + 1) + warp + 1] - gp0 - q0;
+  const int myu = lane < nq ? pair_u[gp0 + q0 + lane] : 0;  // nq <= 27
+  const bool live = lane * 4 < nct;
+  const int c = live ? tile0 + lane * 4 : 0;
+  float2 y[3][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y[i][0] = y[i][1] = make_float2(0.f, 0.f);
+  for (int r0 = 0; r0 < n_r; r0 += rch) {
+    const int nr = min(rch, n_r - r0);
+    if (r0 > 0) __syncthreads();                             // the previous chunk is consumed
+    for (int t = threadIdx.x; t < nr * np * 3; t += GR * 32) {
+      const int rr = t / (np * 3), rem = t - rr * np * 3;
+      cp_async16(ks + (size_t)rr * np * 12 + rem * 4, Kg + ((size_t)(r0 + rr) * n_pairs + gp0) * 12 + rem * 4);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (a < 0) continue;                                     // warp-uniform
+    for (int rr = 0; rr < nr; ++rr) {
+      float2 z[3][2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) z[i][0] = z[i][1] = make_float2(0.f, 0.f);
+      const float* kq = ks + ((size_t)rr * np + q0) * 12;
+#pragma unroll 4
+      for (int i = 0; i < nq; ++i) {
+        const int u = __shfl_sync(0xffffffffu, myu, i);
+        float4 x[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) x[j] = *reinterpret_cast<const float4*>(xs + (size_t)(u * 3 + j) * 128 + lane * 4);
+        float k[12];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          const float4 w = *reinterpret_cast<const float4*>(kq + (size_t)i * 12 + 4 * t);
+          k[4 * t] = w.x; k[4 * t + 1] = w.y; k[4 * t + 2] = w.z; k[4 * t + 3] = w.w;
+        }
+#pragma unroll
+        for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const float kv = k[ii * 3 + j];
+            if (PAIR) {
+              const float2 kk = make_float2(kv, kv);
+              z[ii][0] = __ffma2_rn(kk, make_float2(x[j].x, x[j].y), z[ii][0]);
+              z[ii][1] = __ffma2_rn(kk, make_float2(x[j].z, x[j].w), z[ii][1]);
+            } else {
+              z[ii][0].x = fmaf(kv, x[j].x, z[ii][0].x);
+              z[ii][0].y = fmaf(kv, x[j].y, z[ii][0].y);
+              z[ii][1].x = fmaf(kv, x[j].z, z[ii][1].x);
+              z[ii][1].y = fmaf(kv, x[j].w, z[ii][1].y);
+            }
+          }
+      }
+      const float4 al = __ldg(reinterpret_cast<const float4*>(alpha + (size_t)(r0 + rr) * n_cells + c));
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii) {
+        y[ii][0] = __ffma2_rn(make_float2(al.x, al.y), z[ii][0], y[ii][0]);
+        y[ii][1] = __ffma2_rn(make_float2(al.z, al.w), z[ii][1], y[ii][1]);
+      }
+    }
+  }
+  if (a < 0 || !live) return;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    *reinterpret_cast<float4*>(Y + (size_t)(a * 3 + i) * n_cells + c) = make_float4(y[i][0].x, y[i][0].y, y[i][1].x, y[i][1].y);
+}
+
+// principal blocks [n_r][n_blk][9] -> group order [n_r][n_blk][12] (zero padded, 16-byte rows)
+__global__ void k_group_blocks(int64_t n_blk, int n_r, const int* __restrict__ perm, const float* __restrict__ K,
+                               float* __restrict__ Kg) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= n_blocks * 12) return;
-  const int64_t blk = t / 12;
+  if (t >= (int64_t)n_r * n_blk * 12) return;
+  const int64_t pr = t / 12;
   const int e = (int)(t % 12);
-  Kb[t] = e < 9 ? K[blk * 9 + e] : 0.f;
+  const int64_t r = pr / n_blk, p = pr - r * n_blk;
+  Kg[t] = e < 9 ? K[(r * n_blk + perm[p]) * 9 + e] : 0.f;
+}
+
+constexpr size_t kGroupSmemBudget = 110 * 1024;   // two CTAs per SM
+constexpr size_t kSmemOptin = 227 * 1024;
+
+// shared memory of one CTA for n_r principals (rch of them staged at a time); 0 if it cannot fit
+size_t group_smem(const lat_ctx::NodeGroups& G, int n_r, int* rch) {
+  const size_t xb = (size_t)G.nu_max * 3 * 128 * sizeof(float), kb = (size_t)G.np_max * 12 * sizeof(float);
+  if (xb + kb > kSmemOptin) return 0;
+  const int64_t fit = xb + kb <= kGroupSmemBudget ? (int64_t)((kGroupSmemBudget - xb) / kb) : 1;
+  *rch = (int)std::max<int64_t>(1, std::min<int64_t>(fit, n_r));
+  return xb + (size_t)*rch * kb;
 }
 
 template <typename T, int D, bool FETI>
@@ -326,26 +388,40 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
     dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
-  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0) {
-    // 3D FP32 (measured 2.5x faster than the per-(cell, node) form on the strut lattice; in 2D
-    // the staged form is faster: its 9 neighbour blocks stay in registers across principals)
-    const int64_t nblk = h->nnz / (D * D);
-    const float* Kb = reinterpret_cast<const float*>(Kp);
-    if (D == 3) {
-      if (h->kp12_version != h->sel_version) {
-        const int64_t nb = (int64_t)h->n_r * nblk;
-        h->Kp12.ensure((size_t)nb * 12);
-        LAT_LAUNCH(h, k_pad12<<<div_up(nb * 12, 256), 256, 0, h->stream>>>(nb, h->Kp32.p, h->Kp12.p));
-        h->kp12_version = h->sel_version;
-      }
-      Kb = h->Kp12.p;
+  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0 && h->ng[0].n_grp > 0) {
+    // 3D FP32: node groups staged in shared memory.  Groups of 16 nodes read fewer union rows
+    // per output row and win when the action is one principal over many waves of CTAs (measured
+    // 1.3x faster on 8000 strut cells); groups of 8 keep more CTAs in flight and win otherwise.
+    const int64_t tiles = div_up(h->n_cells, 128);
+    const bool wide = h->n_r == 1 && tiles * h->ng[1].n_grp >= 8LL * h->n_sm;
+    const lat_ctx::NodeGroups& G = h->ng[wide ? 1 : 0];
+    int rch = 1;
+    const size_t shm = group_smem(G, h->n_r, &rch);
+    LAT_REQUIRE(shm > 0, LAT_EINVAL, "node group too large for shared memory");
+    const int64_t nblk = h->n_blk;
+    if (h->kg_version != h->sel_version || h->kg_gr != G.GR) {
+      h->Kg.ensure((size_t)h->n_r * nblk * 12);
+      LAT_LAUNCH(h, k_group_blocks<<<div_up((int64_t)h->n_r * nblk * 12, 256), 256, 0, h->stream>>>(
+                        nblk, h->n_r, G.perm.p, h->Kp32.p, h->Kg.p));
+      h->kg_version = h->sel_version;
+      h->kg_gr = G.GR;
     }
-    dim3 grid(div_up(h->n_cells, 128), div_up(h->n_nodes_cell, 8));
+    const dim3 grid((unsigned)tiles, G.n_grp);
+    const float* al = reinterpret_cast<const float*>(alpha);
+    const float* xx = reinterpret_cast<const float*>(X);
+    float* yy = reinterpret_cast<float*>(Y);
     KernelTimer kt(h, "apply_reduced");
-    LAT_LAUNCH(h, k_apply_v4<D><<<grid, 256, 0, h->stream>>>(h->n_cells, h->n_nodes_cell, h->blk_ptr.p, h->blk_col.p,
-                                                              nblk, h->n_r, Kb, reinterpret_cast<const float*>(alpha),
-                                                              reinterpret_cast<const float*>(X),
-                                                              reinterpret_cast<float*>(Y)));
+    if (G.GR == 16) {
+      LAT_CUDA(cudaFuncSetAttribute(k_apply_groups<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      LAT_LAUNCH(h, k_apply_groups<16, false><<<grid, 16 * 32, shm, h->stream>>>(
+                        h->n_cells, G.rows.p, G.ucptr.p, G.ucol.p, G.pp.p, G.pair_u.p, nblk, h->n_r, rch, h->Kg.p,
+                        al, xx, yy));
+    } else {
+      LAT_CUDA(cudaFuncSetAttribute(k_apply_groups<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      LAT_LAUNCH(h, k_apply_groups<8, true><<<grid, 8 * 32, shm, h->stream>>>(
+                        h->n_cells, G.rows.p, G.ucptr.p, G.ucol.p, G.pp.p, G.pair_u.p, nblk, h->n_r, rch, h->Kg.p,
+                        al, xx, yy));
+    }
   } else {
     KernelTimer kt(h, "apply_reduced");
     if (D == 3 && sizeof(T) == 4) {
@@ -379,6 +455,79 @@ void dispatch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const
 }
 
 }  // namespace
+
+// Node groups for the 3D FP32 action: greedy in node order, each group takes a seed node and then,
+// up to GR nodes, the unassigned neighbour that grows the union of the group's neighbour nodes
+// least (ties: the lowest node).  Every node lies in one group, so the groups' block pairs are a
+// permutation of the block pattern.
+namespace {
+void build_groups(lat_ctx* h, int GR, lat_ctx::NodeGroups& G) {
+  const int nn = h->n_nodes_cell;
+  const auto& bp = h->h_blk_ptr;
+  const auto& bc = h->h_blk_col;
+  auto cols_of = [&](int a) {
+    std::vector<int> W(bc.begin() + bp[a], bc.begin() + bp[a + 1]);
+    std::sort(W.begin(), W.end());
+    return W;
+  };
+  std::vector<char> left(nn, 1);
+  std::vector<int> rows, ucptr{0}, ucol, pp, pair_u, perm;
+  G.GR = GR;
+  G.nu_max = G.np_max = 0;
+  for (int seed = 0; seed < nn; ++seed) {
+    if (!left[seed]) continue;
+    std::vector<int> grp{seed};
+    left[seed] = 0;
+    std::vector<int> U = cols_of(seed);
+    while ((int)grp.size() < GR) {
+      int best = -1;
+      std::vector<int> bestU;
+      for (int b : U) {
+        if (!left[b]) continue;
+        const std::vector<int> W = cols_of(b);
+        std::vector<int> un;
+        std::set_union(U.begin(), U.end(), W.begin(), W.end(), std::back_inserter(un));
+        if (best < 0 || un.size() < bestU.size()) {
+          best = b;
+          bestU.swap(un);
+        }
+      }
+      if (best < 0) break;
+      grp.push_back(best);
+      left[best] = 0;
+      U.swap(bestU);
+    }
+    const int base = (int)perm.size();
+    for (int q = 0; q < GR; ++q) {
+      rows.push_back(q < (int)grp.size() ? grp[q] : -1);
+      pp.push_back((int)perm.size());
+      if (q >= (int)grp.size()) continue;
+      for (int bi = bp[grp[q]]; bi < bp[grp[q] + 1]; ++bi) {
+        pair_u.push_back((int)(std::lower_bound(U.begin(), U.end(), bc[bi]) - U.begin()));
+        perm.push_back(bi);
+      }
+    }
+    pp.push_back((int)perm.size());
+    G.np_max = std::max(G.np_max, (int)perm.size() - base);
+    G.nu_max = std::max(G.nu_max, (int)U.size());
+    ucol.insert(ucol.end(), U.begin(), U.end());
+    ucptr.push_back((int)ucol.size());
+  }
+  G.n_grp = (int)ucptr.size() - 1;
+  G.rows.upload(rows, h->stream);
+  G.ucptr.upload(ucptr, h->stream);
+  G.ucol.upload(ucol, h->stream);
+  G.pp.upload(pp, h->stream);
+  G.pair_u.upload(pair_u, h->stream);
+  G.perm.upload(perm, h->stream);
+  LAT_CUDA(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+}
+}  // namespace
+
+void build_node_groups(lat_ctx* h) {
+  build_groups(h, 8, h->ng[0]);
+  build_groups(h, 16, h->ng[1]);
+}
 
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti) {
   LAT_REQUIRE(h->n_r > 0 && h->Kp.p, LAT_EINVAL, "no principal cells selected");

@@ -144,8 +144,20 @@ struct lat_ctx {
   DBuf<float> alpha32;
   DBuf<double> Kp;                    // [n_r][nnz]
   DBuf<float> Kp32;
-  DBuf<float> Kp12;                     // 3D FP32 principal blocks padded to 12 values
-  int64_t sel_version = 0, kp12_version = -1;   // principal-set changes / the padded copy's
+  // 3D FP32 reduced action: the cell's nodes in groups of GR = 8 and 16 (one CTA each), with the
+  // union of each group's neighbour nodes and its node blocks in group order (built at setup)
+  struct NodeGroups {
+    int GR = 0, n_grp = 0, nu_max = 0, np_max = 0;
+    DBuf<int> rows;    // [n_grp][GR] node of each warp, -1 for none
+    DBuf<int> ucptr;   // [n_grp + 1] into ucol
+    DBuf<int> ucol;    // union of the group's neighbour nodes, ascending
+    DBuf<int> pp;      // [n_grp][GR + 1] block ranges of the group's rows (global block-pair index)
+    DBuf<int> pair_u;  // [n_blk] position of the pair's column node in its group's union
+    DBuf<int> perm;    // [n_blk] CSR block index of each pair
+  } ng[2];
+  DBuf<float> Kg;                     // [n_r][n_blk][12] FP32 principal blocks in group order
+  int64_t sel_version = 0, kg_version = -1;   // principal-set changes / the group-order copy's
+  int kg_gr = 0;
   // greedy workspaces
   DBuf<double> g_delta, g_Z, g_beta, g_inf, g_nrm2, g_norms, g_part, g_maxres;
   DBuf<int> g_state;                  // [0] done, [1] n_r, [2] s_next
@@ -348,6 +360,7 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
                 int* S_out, int* n_r_out, double* alpha_out, double* beta_out, double* Z_out,
                 double* max_res_host);
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti);
+void build_node_groups(lat_ctx* h);
 void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
 // square tile (64, 32 or 16) for batched FP64 products over n x n matrices: the least padded
 // work per busy SM (padding of n to the tile, and the share of the SMs the tiles occupy)

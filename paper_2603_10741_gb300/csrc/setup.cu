@@ -139,6 +139,7 @@ void build_pattern_and_colors(lat_ctx* h, const int* E) {
   h->elem_blk.upload(eb, h->stream);
   h->blk_ptr.upload(h->h_blk_ptr, h->stream);
   h->blk_col.upload(h->h_blk_col, h->stream);
+  if (h->dim == 3) build_node_groups(h);
   // greedy colouring: elements of one colour share no node
   std::vector<std::vector<int>> node_el(nn);
   for (int e = 0; e < h->n_el; ++e)
@@ -595,7 +596,8 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->cell_class);
   rel(h->coarse_ptr); rel(h->coarse_src); rel(h->cb_dest); rel(h->cb_perm); rel(h->cb_A);
   rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->coarse_row); rel(h->coarse_col);
-  rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32); rel(h->Kp12);
+  rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32); rel(h->Kg);
+  for (auto& g : h->ng) { rel(g.rows); rel(g.ucptr); rel(g.ucol); rel(g.pp); rel(g.pair_u); rel(g.perm); }
   rel(h->g_delta); rel(h->g_Z); rel(h->g_beta); rel(h->g_inf); rel(h->g_nrm2); rel(h->g_norms);
   rel(h->g_part); rel(h->g_maxres); rel(h->g_state); rel(h->g_scale);
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);

@@ -278,9 +278,9 @@ def test_set_principal_cells_apply(L, name, n_r):
 
 @pytest.mark.parametrize("dims", [(3, 1, 1), (2, 2, 1), (1, 1, 5)])
 def test_apply_ragged_3d_cell_counts(L, dims):
-    """3D strut lattices with 3, 4 and 5 cells: the FP32 action takes the 16-byte four-cell path
-    only when the cell count is a multiple of four and the per-(cell, node) path otherwise; both
-    must equal the oracle's sum_r alpha_r^s K^r x_s (caller-given principals and coefficients)."""
+    """3D strut lattices with 3, 4 and 5 cells: the FP32 action takes the node-group path only
+    when the cell count is a multiple of four and the per-(cell, node) path otherwise; both must
+    equal the oracle's sum_r alpha_r^s K^r x_s (caller-given principals and coefficients)."""
     Xr, E = latgen.strut_cell(6, 0.2)
     lat_geo = latgen.tile(Xr, E, dims)
     n = lat_geo.n_cells
@@ -299,4 +299,35 @@ def test_apply_ragged_3d_cell_counts(L, dims):
         lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor(S), torch.tensor(al))
         Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=dt)).cpu().numpy()
         assert _rel(Y, Y_ref) < tol
+        lat.close()
+
+
+@pytest.mark.parametrize("dims,n_r", [((5, 4, 7), 7), ((15, 14, 14), 1)])
+def test_apply_node_groups(L, dims, n_r):
+    """The FP32 node-group action on 12^3-voxel strut cells (2640 local DOF):
+    140 cells (one full and one partial 128-cell tile) with 7 principals, whose blocks are staged
+    in two chunks of shared memory (5 per chunk for the 8-node groups); and 2940 cells with one
+    principal, which takes the 16-node groups (23 tiles x 55 groups >= 8 CTAs per SM on 152 SMs).
+    Both equal the oracle's sum_r alpha_r^s K^r x_s on sampled cells, the partial tile's included;
+    the FP64 action of the same handle pins the same cells to rounding."""
+    Xr, E = latgen.strut_cell(12, 0.15)
+    lat_geo = latgen.tile(Xr, E, dims)
+    n = lat_geo.n_cells
+    assert n % 4 == 0
+    case = latgen.LoadCase(name="strut-groups", lattice=lat_geo, mu=1.0, lam=4.0,
+                           mu_scale=latgen.mu_scale(n, 11), total_strain=0.05, n_steps=5, eps=5e-3)
+    prob = Problem(case)
+    u = _state(case, 0.01, 25)
+    S = np.arange(n_r, dtype=np.int32) * 3
+    al = latgen.dirichlet_coefficients(n_r, n, 12)
+    Kp = OC.tangent(prob.cell, prob.local(u)[S], prob.mu_cells[S], prob.lam)
+    X = latgen.uniform_field((prob.cell.n_nodes * 3, n), 26)
+    rng = np.random.default_rng(27)
+    cells = np.unique(np.concatenate([rng.choice(n, 40, replace=False), np.arange(n - 8, n), [0, 127, 128]]))
+    Y_ref = OR.reduced_apply(prob.cell, Kp, al[:, cells], X[:, cells])
+    for prec, dt, tol in ((0, torch.float64, 1e-10), (1, torch.float32, 2e-6)):
+        lat = L.Lattice.from_case(case, prec)
+        lat.set_principal_cells(torch.tensor(u, device="cuda"), torch.tensor(S), torch.tensor(al))
+        Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=dt)).cpu().numpy()
+        assert _rel(Y[:, cells], Y_ref) < tol
         lat.close()
