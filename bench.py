@@ -214,7 +214,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 KERNELS = ["residual", "tangent_full", "tangent_reduced", "greedy_update", "apply_reduced", "apply_percell",
            "local_segmm", "local_gemv", "local_tc", "gj_update", "gj_pivot", "densify", "phi_schur",
-           "coarse_blocked", "coarse_gemv", "local_segmm_dual", "local_gemv_dual", "local_tc_dual",
+           "coarse_blocked", "coarse_gemv", "coarse_solve", "local_segmm_dual", "local_gemv_dual", "local_tc_dual",
            "local_segmm_dual_in", "local_gemv_dual_in", "local_tc_dual_in", "dual_schur", "krylov_orth"]
 
 
@@ -230,7 +230,9 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
     apply_percell: the plain path, 8 nnz bytes of K^s and the two vectors per cell;
     coarse_gemv: the explicit coarse inverse streamed once: FP64 (2 n_primal^2 flops, FP64-ALU
         bound on GB300: one multiply-add per 8 bytes is above its FP64 rate) or, in the mixed
-        modes, its FP32 copy (4 n_primal^2 bytes, HBM bound).
+        modes, its FP32 copy (4 n_primal^2 bytes, HBM bound);
+    coarse_solve: the FP64 block-LU solve of the block-tridiagonal coarse matrix, N blocks of
+        size m: two sweeps of N - 1 block products and one of N, 2 (3 N - 2) m^2 flops.
     """
     n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
     n_rr, n_p = s.n_r_local, s.n_p_local
@@ -247,6 +249,9 @@ def kernel_work(name, s, n_r, n_keys, prec_bytes, mixed=False):
         return 2.0 * n_r * nnz * n_s, "flops"
     if name == "apply_percell":
         return 8.0 * nnz * n_s + 2 * 8.0 * n_loc * n_s, "bytes"
+    if name == "coarse_solve" and s.n_coarse_blocks:
+        nb, mb = s.n_coarse_blocks, s.coarse_block
+        return 2.0 * (3 * nb - 2) * mb * mb, "flops"
     if name == "coarse_gemv":
         if mixed:
             return 4.0 * s.n_primal * s.n_primal + 16.0 * s.n_primal, "bytes"
@@ -390,7 +395,7 @@ def run_ours(args):
                    "kernels": kt_red},
     }
     # roofline of every modelled kernel; the headline entry is the one with the largest share
-    rl = kernel_rooflines(kt_red, s, out["newton"]["n_r"],
+    rl = kernel_rooflines(kt_red, lat.sizes, out["newton"]["n_r"],
                           FP64_PEAK_TFLOPS if args.precision == "fp64" else FP32_PEAK_TFLOPS, hbm_peak, bf16_peak,
                           mixed=args.precision != "fp64")
     if rl:

@@ -94,6 +94,12 @@ typedef struct {
   int32_t n_q_reduced;  /* quadrature points per cell, reduced (snapshot) rule */
   int32_t n_i_local;    /* remaining DOFs per cell off the cell boundary; the other n_r_local -
                            n_i_local remaining DOFs are the dual (interface) DOFs */
+  int32_t n_coarse_blocks; /* diagonal blocks of the block-tridiagonal coarse matrix (cell layers
+                              along the load axis), 0 when it is not block tridiagonal */
+  int32_t coarse_block;    /* their common padded size */
+  int32_t coarse_block_lu; /* 1 when the FP64 coarse solves run as block LU (two sequential
+                              sweeps over the blocks, no explicit inverse), 0 when they apply the
+                              explicit inverse; set by lattice_prepare_solver */
 } lat_sizes;
 
 /* Setup: uploads the reference cell, the maps and the boundary data, builds the local pattern,
@@ -204,6 +210,12 @@ typedef struct {
                               principal's remaining block is not positive definite, primal
                               nodes are added on every cell edge (level L: the nodes nearest to
                               the points j/2^L of each edge) for all cells, and kept */
+  int32_t coarse_block_lu; /* coarse solves of a block-tridiagonal coarse matrix: 1 block LU in
+                              FP64 (two sequential sweeps over the cell layers, factors N m^3,
+                              no explicit inverse), 0 the explicit inverse (N^2 m^3 to build,
+                              one dense product per solve; FP32 copy in the mixed modes), -1
+                              (default) block LU when the explicit inverse would hold more than
+                              8192^2 entries (N blocks of size m, N m > 8192) */
 } lat_newton_opts;
 
 typedef struct {

@@ -13,10 +13,23 @@
 // at a cost of about N^2 m^3 instead of the (N m)^3 of a dense inversion.  The forward and the
 // backward recurrence are independent; they advance together, one step of each per batched
 // launch.  Blocks are stored padded to a common size m (identity on the padding); the result is
-// scattered into the dense inverse used by the coarse solves.
+// scattered into the dense inverse used by the mixed-precision coarse solves.
+//
+// The FP64 solves use the forward factors alone (block LU, no inverse formed):
+//   y_0 = g_0,   y_i = g_i - U_{i-1}^T y_{i-1}        (U_i^T = B_i^T D_i^{-1}, D_i symmetric)
+//   w_i = D_i^{-1} y_i                                 (all blocks at once)
+//   x_{N-1} = w_{N-1},   x_i = w_i - U_i x_{i+1}
+// which is 3 N m^2 multiply-adds per solve instead of N^2 m^2.  The two sweeps are sequential
+// in i; each runs in one thread-block cluster (16 CTAs where the device allows it, else 8) that
+// splits the m rows of every step, prefetches the next step's rows with cp.async and exchanges
+// the new block vector through distributed shared memory, one cluster barrier per step.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -166,9 +179,155 @@ void bgemm(lat_ctx* h, int m, std::vector<const double*> a, std::vector<const do
   }
 }
 
+__device__ __forceinline__ void cp_async8(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One sweep of the block-LU solve in one cluster.  Step s handles block b = s (forward) or
+// N-1-s (backward): v_b = rhs_b - M_s v_prev with M_s = U_{b-1}^T (forward, stored transposed as
+// Ut) or U_b (backward), and v_b = rhs_b at step 0.  CTA c of the cluster owns rows
+// [c R, c R + R) of every block.  Its rows' right-hand sides for all blocks are loaded once at
+// the start, the next step's matrix rows are prefetched with cp.async, and each new value is
+// stored straight into every peer's copy of the block vector (distributed shared memory, two
+// copies alternating by step), so that a step is one cluster barrier and no remote load; the
+// results stay in shared memory until the last step (a global store before the barrier would
+// put its L2 round trip on every step).  The
+// forward sweep reads rhs from the primal vector g through perm (0 on padding) and writes y in
+// block layout; the backward sweep reads w in block layout and scatters x to the primal vector.
+template <bool FWD>
+__global__ void __launch_bounds__(256)
+    k_coarse_sweep(int N, int m, int R, const double* __restrict__ Mblk, const double* __restrict__ rhs,
+                   const int* __restrict__ perm, double* __restrict__ out, int pre) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int c = (int)cl.block_rank(), C = (int)cl.num_blocks();
+  extern __shared__ __align__(16) double csm[];
+  const int mp = (m + 1) & ~1, Rp = (R + 1) & ~1;
+  double* vbuf = csm;                   // [2][mp] block vector of the previous step, by parity
+  double* rs = csm + 2 * mp;            // [N][Rp] this CTA's right-hand sides
+  double* os = rs + (size_t)N * Rp;     // [N][Rp] this CTA's results (written out at the end)
+  double* Ms = os + (size_t)N * Rp;     // [2][R][m] prefetched rows (pre)
+  const int r0 = c * R, nr = max(0, min(R, m - r0));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t mm = (size_t)m * m;
+  auto mat = [&](int st) { return Mblk + (size_t)(FWD ? st - 1 : N - 1 - st) * mm + (size_t)r0 * m; };
+  auto put = [&](int b, int r, double v) {
+    if (FWD) out[(size_t)b * m + r] = v;
+    else {
+      const int p = perm[(size_t)b * m + r];
+      if (p >= 0) out[p] = v;
+    }
+  };
+  auto prefetch = [&](int st) {
+    const double* src = mat(st);
+    double* dst = Ms + (size_t)(st & 1) * R * m;
+    for (int t = threadIdx.x; t < nr * m; t += blockDim.x) cp_async8(dst + t, src + t);
+    cp_async_commit();
+  };
+  if (pre) {
+    if (N > 1) prefetch(1);
+    else cp_async_commit();
+  }
+  for (int t = threadIdx.x; t < N * nr; t += blockDim.x) {
+    const int b = t / nr, lr = t - b * nr;
+    double v;
+    if (FWD) {
+      const int p = perm[(size_t)b * m + r0 + lr];
+      v = p >= 0 ? rhs[p] : 0.0;
+    } else {
+      v = rhs[(size_t)b * m + r0 + lr];
+    }
+    rs[(size_t)b * Rp + lr] = v;
+  }
+  __syncthreads();
+  {
+    const int b = FWD ? 0 : N - 1;
+    for (int t = threadIdx.x; t < nr * C; t += blockDim.x) {
+      const int lr = t / C, q = t - lr * C;
+      const double v = rs[(size_t)b * Rp + lr];
+      cl.map_shared_rank(vbuf, q)[r0 + lr] = v;
+      if (q == 0) os[(size_t)b * Rp + lr] = v;
+    }
+  }
+  cl.sync();
+  for (int st = 1; st < N; ++st) {
+    if (pre) {
+      if (st + 1 < N) prefetch(st + 1);
+      else cp_async_commit();
+      cp_async_wait_1();
+      __syncthreads();
+    }
+    const int b = FWD ? st : N - 1 - st;
+    const double* vin = vbuf + (size_t)((st - 1) & 1) * mp;
+    const size_t vout = (size_t)(st & 1) * mp;
+    for (int lr = warp; lr < nr; lr += nw) {
+      const double* Mrow = pre ? Ms + (size_t)(st & 1) * R * m + (size_t)lr * m : mat(st) + (size_t)lr * m;
+      double a0 = 0.0, a1 = 0.0;
+      int k = lane;
+      for (; k + 32 < m; k += 64) {
+        a0 = fma(Mrow[k], vin[k], a0);
+        a1 = fma(Mrow[k + 32], vin[k + 32], a1);
+      }
+      if (k < m) a0 = fma(Mrow[k], vin[k], a0);
+      const double v = rs[(size_t)b * Rp + lr] - warp_sum(a0 + a1);   // every lane holds the sum
+      if (lane < C) cl.map_shared_rank(vbuf, lane)[vout + r0 + lr] = v;
+      if (lane == 0) os[(size_t)b * Rp + lr] = v;
+    }
+    cl.sync();   // only shared-memory stores precede it: no global store on the step's path
+  }
+  if (pre) cp_async_wait_0();
+  for (int t = threadIdx.x; t < N * nr; t += blockDim.x) {
+    const int b = t / nr, lr = t - b * nr;
+    put(b, r0 + lr, os[(size_t)b * Rp + lr]);
+  }
+}
+
+// w_t = (D_b^{-1} y_b)_l for every row t = b m + l of the block layout (one warp per row)
+__global__ void __launch_bounds__(256) k_coarse_dinv(int N, int m, const double* __restrict__ Dinv,
+                                                     const double* __restrict__ y, double* __restrict__ w) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= (int64_t)N * m) return;
+  const int64_t b = t / m, l = t - b * m;
+  const double* row = Dinv + (size_t)b * m * m + (size_t)l * m;
+  const double* yb = y + (size_t)b * m;
+  double acc = 0.0;
+  for (int k = lane; k < m; k += 32) acc = fma(row[k], yb[k], acc);
+  acc = warp_sum(acc);
+  if (lane == 0) w[t] = acc;
+}
+
+template <bool FWD>
+void launch_sweep(lat_ctx* h, const double* M, const double* rhs, double* out) {
+  const int C = h->cb_cluster, R = div_up(h->cb_m, C);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = h->cb_shm;
+  cfg.stream = h->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  LAT_LAUNCH(h, LAT_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_sweep<FWD>, h->cb_n, h->cb_m, R, M, rhs,
+                                            (const int*)h->cb_perm.p, out, h->cb_pre)));
+}
+
 }  // namespace
 
-void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
+void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense) {
   const int N = h->cb_n, m = h->cb_m;
   const size_t mm = (size_t)m * m;
   const int N1 = std::max(1, N - 1);
@@ -179,8 +338,9 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
   h->cb_Einv.ensure((size_t)N1 * mm);      // B_i^T
   h->cb_U.ensure((size_t)N1 * mm);         // D_i^-1 B_i  (= -U_i)
   h->cb_T.ensure((size_t)N1 * mm);         // E_{i+1}^-1 B_i^T
-  h->cb_X.ensure((size_t)N * N * mm);
-  double *DE = h->cb_Dinv.p, *Bt = h->cb_Einv.p, *U = h->cb_U.p, *T = h->cb_T.p, *X = h->cb_X.p;
+  if (dense) h->cb_X.ensure((size_t)N * N * mm);
+  else h->cb_X.release();
+  double *DE = h->cb_Dinv.p, *Bt = h->cb_Einv.p, *U = h->cb_U.p, *T = h->cb_T.p, *X = h->cb_X.p;   // X: dense only
   const int64_t half = (int64_t)N * mm;    // stride from D_k^-1 to the k-th backward inverse
   auto blk = [&](double* base, int i) { return base + (size_t)i * mm; };
   auto erev = [&](int k) { return DE + half + (size_t)k * mm; };   // E_{N-1-k}^-1
@@ -197,6 +357,26 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
     LAT_LAUNCH(h, k_transpose_blocks<<<div_up((int64_t)(N - 1) * mm, 256), 256, 0, h->stream>>>(N - 1, m, Bk, Bt));
   LAT_CHECK_LAUNCH();
   (void)S;
+  if (!dense) {
+    // forward recurrence only: D_i^{-1} in place, U_{i-1} = D_{i-1}^{-1} B_{i-1}
+    cpy(blk(DE, 0), blk(A, 0));
+    gj_invert(h, DE, m, 1, (int64_t)mm, 8);
+    for (int i = 1; i < N; ++i) {
+      bgemm<false, false>(h, m, {blk(DE, i - 1)}, {blk(Bk, i - 1)}, {blk(U, i - 1)}, 1.0, 0.0);
+      cpy(blk(DE, i), blk(A, i));
+      bgemm<false, false>(h, m, {blk(Bt, i - 1)}, {blk(U, i - 1)}, {blk(DE, i)}, -1.0, 1.0);
+      gj_invert(h, blk(DE, i), m, 1, (int64_t)mm, 8);
+    }
+    // U_i^T for the forward sweep, and the sweep buffers
+    h->cb_Ut.ensure((size_t)N1 * mm);
+    if (N > 1)
+      LAT_LAUNCH(h, k_transpose_blocks<<<div_up((int64_t)(N - 1) * mm, 256), 256, 0, h->stream>>>(N - 1, m, U,
+                                                                                                   h->cb_Ut.p));
+    h->cb_y.ensure((size_t)N * m);
+    h->cb_w.ensure((size_t)N * m);
+    LAT_CHECK_LAUNCH();
+    return;
+  }
   // step 0: D_0 = A_0 (kept in X_00 until the diagonal update), E_{N-1} = A_{N-1}
   cpy(xb(0, 0), blk(A, 0));
   cpy(blk(DE, 0), blk(A, 0));
@@ -240,4 +420,62 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np) {
   LAT_LAUNCH(h, k_scatter_inverse<<<div_up(tot, 256), 256, 0, h->stream>>>(N, m, h->cb_perm.p, X, np,
                                                                             h->CoarseInv.p));
   LAT_CHECK_LAUNCH();
+}
+
+// Cluster size and shared memory of the FP64 block-LU sweeps; false when the device runs no
+// cluster of at least 8 CTAs with them (the dense inverse is used then).
+bool coarse_block_plan(lat_ctx* h) {
+  const int m = h->cb_m;
+  for (int C : {16, 8}) {
+    const int R = div_up(m, C);
+    const int mp = (m + 1) & ~1, Rp = (R + 1) & ~1;
+    const size_t base = (size_t)(2 * mp + 2 * (size_t)h->cb_n * Rp) * sizeof(double);
+    size_t shm = base + 2 * (size_t)R * m * sizeof(double);
+    int pre = 1;
+    if (shm > 200 * 1024) {
+      shm = base;
+      pre = 0;
+    }
+    if (shm > 200 * 1024) continue;
+    bool ok = true;
+    for (auto fn : {(const void*)k_coarse_sweep<true>, (const void*)k_coarse_sweep<false>}) {
+      if (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) ok = false;
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess) ok = false;
+    }
+    if (ok) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = shm;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      ok = cudaOccupancyMaxActiveClusters(&n, k_coarse_sweep<true>, &cfg) == cudaSuccess && n >= 1;
+    }
+    cudaGetLastError();   // a refused size is not an error of the library
+    if (ok) {
+      h->cb_cluster = C;
+      h->cb_shm = shm;
+      h->cb_pre = pre;
+      return true;
+    }
+  }
+  h->cb_cluster = 0;
+  return false;
+}
+
+// x_P = S_PP^{-1} g_P by the block-LU sweeps (FP64)
+void run_coarse_block_solve(lat_ctx* h, const double* g, double* x) {
+  const int N = h->cb_n, m = h->cb_m;
+  launch_sweep<true>(h, h->cb_Ut.p, g, h->cb_y.p);
+  const int64_t rows = (int64_t)N * m;
+  LAT_LAUNCH(h, k_coarse_dinv<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv.p, h->cb_y.p,
+                                                                             h->cb_w.p));
+  LAT_CHECK_LAUNCH();
+  launch_sweep<false>(h, h->cb_U.p, h->cb_w.p, x);
 }

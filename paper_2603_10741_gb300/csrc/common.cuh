@@ -131,10 +131,14 @@ struct lat_ctx {
   // axis); empty when the lattice does not give one
   bool coarse_blocked = false;
   int cb_n = 0, cb_m = 0;                 // number of blocks, padded block size
+  bool cb_solve = false;                  // FP64 coarse solves by block LU (no dense inverse)
+  int cb_cluster = 0, cb_pre = 0;         // CTAs per cluster of the sweeps, rows prefetched
+  size_t cb_shm = 0;
   DBuf<int64_t> cb_dest;                  // coarse entry -> index in [A blocks | B blocks], -1 skip
   DBuf<int> cb_perm;                      // block position (b*m + l) -> primal DOF or -1
   std::vector<int32_t> h_cell_layer;
   DBuf<double> cb_A, cb_B, cb_Dinv, cb_Einv, cb_U, cb_V, cb_T, cb_X;
+  DBuf<double> cb_Ut, cb_y, cb_w;       // block-LU solves: U_i^T, forward result, D^-1 y
 
   // selection state
   int n_r = 0;
@@ -399,7 +403,10 @@ void build_feti(lat_ctx* h, int level);
 void prepare_enriched(lat_ctx* h, const lat_newton_opts* o);
 void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit, int split = -1,
                double* snap = nullptr);
-void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np);
+void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
+bool coarse_block_plan(lat_ctx* h);
+constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
+void run_coarse_block_solve(lat_ctx* h, const double* g, double* x);
 void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)
 enum KinvMode { KINV_FULL = 0, KINV_DUAL = 1, KINV_DUAL_IN = 2 };

@@ -595,7 +595,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->p_copy_ptr); rel(h->p_copy); rel(h->loc_fixed); rel(h->lam_p); rel(h->lam_m);
   rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->cell_class);
   rel(h->coarse_ptr); rel(h->coarse_src); rel(h->cb_dest); rel(h->cb_perm); rel(h->cb_A);
-  rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->coarse_row); rel(h->coarse_col);
+  rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->cb_Ut); rel(h->cb_y); rel(h->cb_w); rel(h->coarse_row); rel(h->coarse_col);
   rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32); rel(h->Kg);
   for (auto& g : h->ng) { rel(g.rows); rel(g.ucptr); rel(g.ucol); rel(g.pp); rel(g.pair_u); rel(g.perm); }
   rel(h->g_delta); rel(h->g_Z); rel(h->g_beta); rel(h->g_inf); rel(h->g_nrm2); rel(h->g_norms);
@@ -637,6 +637,9 @@ extern "C" lat_status lattice_sizes(lat_handle h, lat_sizes* o) {
   o->n_q_full = h->nq[0] * h->n_el;
   o->n_q_reduced = h->nq[1] * h->n_el;
   o->n_i_local = h->n_I;
+  o->n_coarse_blocks = h->coarse_blocked ? h->cb_n : 0;
+  o->coarse_block = h->coarse_blocked ? h->cb_m : 0;
+  o->coarse_block_lu = h->cb_solve ? 1 : 0;
   return LAT_OK;
 }
 

@@ -47,7 +47,8 @@ class Sizes(C.Structure):
                 ("n_blocks", C.c_int32), ("nnz", C.c_int64), ("n_r_local", C.c_int32),
                 ("n_p_local", C.c_int32), ("n_primal", C.c_int64), ("n_lambda", C.c_int64),
                 ("n_krylov", C.c_int64), ("n_q_full", C.c_int32), ("n_q_reduced", C.c_int32),
-                ("n_i_local", C.c_int32)]
+                ("n_i_local", C.c_int32), ("n_coarse_blocks", C.c_int32), ("coarse_block", C.c_int32),
+                ("coarse_block_lu", C.c_int32)]
 
 
 class NewtonOpts(C.Structure):
@@ -55,7 +56,7 @@ class NewtonOpts(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("krylov_rtol", C.c_double),
                 ("krylov_max_it", C.c_int32), ("krylov_restart", C.c_int32), ("pcg_iters", C.c_int32),
                 ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32),
-                ("max_enrich", C.c_int32)]
+                ("max_enrich", C.c_int32), ("coarse_block_lu", C.c_int32)]
 
 
 class NewtonReport(C.Structure):
