@@ -381,23 +381,42 @@ size_t group_smem(const lat_ctx::NodeGroups& G, int n_r, int* rch) {
   return xb + (size_t)*rch * kb;
 }
 
+struct GroupPlan {
+  const lat_ctx::NodeGroups* G = nullptr;
+  int rch = 1;
+  size_t shm = 0;
+};
+
+// Groups of 16 nodes read fewer union rows per output row and win when the action is one
+// principal over many waves of CTAs (measured 1.3x faster on 8000 strut cells); groups of 8 keep
+// more CTAs in flight and win otherwise.  False when no group size fits in shared memory (the
+// per-(cell, node) kernel runs then).
+bool group_plan(lat_ctx* h, GroupPlan* p) {
+  if (h->ng[0].n_grp == 0) return false;
+  const int64_t tiles = div_up(h->n_cells, 128);
+  const bool wide = h->n_r == 1 && tiles * h->ng[1].n_grp >= 8LL * h->n_sm;
+  for (int k : {wide ? 1 : 0, 0}) {
+    p->G = &h->ng[k];
+    p->shm = group_smem(*p->G, h->n_r, &p->rch);
+    if (p->shm > 0) return true;
+  }
+  return false;
+}
+
 template <typename T, int D, bool FETI>
 void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T* X, T* Y) {
+  GroupPlan gp;
   if (h->force_all) {
     dim3 blk(32, 8);
     dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
     KernelTimer kt(h, "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
-  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0 && h->ng[0].n_grp > 0) {
-    // 3D FP32: node groups staged in shared memory.  Groups of 16 nodes read fewer union rows
-    // per output row and win when the action is one principal over many waves of CTAs (measured
-    // 1.3x faster on 8000 strut cells); groups of 8 keep more CTAs in flight and win otherwise.
+  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0 && group_plan(h, &gp)) {
+    // 3D FP32: node groups staged in shared memory
+    const lat_ctx::NodeGroups& G = *gp.G;
+    const int rch = gp.rch;
+    const size_t shm = gp.shm;
     const int64_t tiles = div_up(h->n_cells, 128);
-    const bool wide = h->n_r == 1 && tiles * h->ng[1].n_grp >= 8LL * h->n_sm;
-    const lat_ctx::NodeGroups& G = h->ng[wide ? 1 : 0];
-    int rch = 1;
-    const size_t shm = group_smem(G, h->n_r, &rch);
-    LAT_REQUIRE(shm > 0, LAT_EINVAL, "node group too large for shared memory");
     const int64_t nblk = h->n_blk;
     if (h->kg_version != h->sel_version || h->kg_gr != G.GR) {
       h->Kg.ensure((size_t)h->n_r * nblk * 12);
