@@ -13,6 +13,10 @@
 // values (corners, and edge nodes after enrichment) come from the global primal vector through
 // the cell's primal map; outputs at fixed local DOFs are zeroed, outputs at primal rows are kept
 // for the primal assembly.
+#include <algorithm>
+#include <iterator>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
