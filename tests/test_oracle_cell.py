@@ -113,9 +113,7 @@ def test_snapshot_is_reduced_rule_tangent():
     # one-point rule: the element matrix is the centre-point integrand times the element area
     Kbar = C.tangent(cell, u, np.ones(3), 4.0, reduced=True)
     assert np.array_equal(T, Kbar.T)
-    Kfull = C.tangent(cell, u, np.ones(3), 4.0)
-    rel = np.abs(Kbar - Kfull).max() / np.abs(Kfull).max()
-    assert 1e-4 < rel < 0.5            # an under-integrated, but close, tangent
+    # the one-point rule itself is pinned to a closed form below
 
 
 def test_pattern_covers_element_pairs():
@@ -124,3 +122,54 @@ def test_pattern_covers_element_pairs():
     assert cell.nnz == 2496
     X, E = latgen.ring_cell(16)
     assert C.RefCell(X, E).nnz == 9600
+
+
+def _q1_corners(d):
+    """Q1 node positions xi_a in [-1,1]^d: counter-clockwise, bottom face then top face."""
+    sq = [(-1, -1), (1, -1), (1, 1), (-1, 1)]
+    if d == 2:
+        return np.array(sq, dtype=float)
+    return np.array([p + (z,) for z in (-1, 1) for p in sq], dtype=float)
+
+
+def _one_point_stiffness(A, d, mu, lam):
+    """Linear-elastic Q1 stiffness of the affine element X = X0 + A xi integrated with the single
+    centre point (weight 2^d on [-1,1]^d): K = 2^d |det A| B(0)^T C B(0), with Voigt B(0) built
+    from the centre gradients grad_xi phi_a(0) = xi_a / 2^d mapped by A^{-T}."""
+    nodes = _q1_corners(d)
+    Ainv_T = np.linalg.inv(A).T
+    nv = 3 if d == 2 else 6
+    Cv = np.zeros((nv, nv))
+    Cv[:d, :d] = lam
+    Cv[range(d), range(d)] += 2 * mu
+    Cv[range(d, nv), range(d, nv)] = mu
+    shear = [(0, 1)] if d == 2 else [(1, 2), (0, 2), (0, 1)]
+    B = np.zeros((nv, 2 ** d * d))
+    for a, xa in enumerate(nodes):
+        g = Ainv_T @ (xa / 2 ** d)
+        for k in range(d):
+            B[k, a * d + k] = g[k]
+        for v, (i, j) in enumerate(shear):
+            B[d + v, a * d + i] = g[j]
+            B[d + v, a * d + j] = g[i]
+    return 2 ** d * abs(np.linalg.det(A)) * B.T @ Cv @ B
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_one_point_rule_matches_closed_form_on_a_skewed_element(d):
+    """Eq. (snapshots) with the one-point rule: at rest, the reduced-rule tangent of a skewed
+    (affine, non-rectangular) element equals the hand-written centre-point stiffness; the
+    full 2^d rule differs from it (the hourglass modes are stiff there)."""
+    A = np.array([[0.5, 0.15], [0.05, 0.4]]) if d == 2 else \
+        np.array([[0.5, 0.1, 0.05], [0.02, 0.45, 0.1], [0.08, 0.03, 0.4]]) / 2
+    X = 0.3 + _q1_corners(d) @ A.T           # element node positions X_a = X0 + A xi_a
+    E = np.arange(2 ** d)[None, :]
+    cell = C.RefCell(X, E)
+    zero = np.zeros((1, 2 ** d, d))
+    K1 = cell.dense(C.tangent(cell, zero, np.array([1.3]), 4.0, reduced=True)[0])
+    ref = _one_point_stiffness(A, d, 1.3, 4.0)
+    assert np.abs(K1 - ref).max() < 1e-13 * np.abs(ref).max()
+    K2 = cell.dense(C.tangent(cell, zero, np.array([1.3]), 4.0)[0])
+    assert np.abs(K2 - ref).max() > 1e-2 * np.abs(ref).max()
+    # one point sees only the centre strain: the rank is the number of strain components
+    assert np.linalg.matrix_rank(K1, tol=1e-10 * np.abs(K1).max()) == (3 if d == 2 else 6)
