@@ -148,10 +148,10 @@ lat_status greedy_select(lat_handle h, const double* T, int64_t n_rows, int32_t 
                          int32_t max_nr, int32_t* S, int32_t* n_r, double* alpha, double* beta,
                          double* Z, double* max_res);
 
-/* Allocation-free Algorithm 1 for callers that cannot allocate device memory (a memory arena
- * that owns the device budget, a host application that forbids cudaMalloc/cudaFree, code that
- * cannot create a handle since lattice_setup allocates).  The paper has no counterpart: this
- * is a library variant of greedy_select.  Same arguments and results as greedy_select for
+/* Allocation-free variant of greedy_select, for callers that cannot allocate device memory (a
+ * memory arena that owns the device budget, a host application that forbids cudaMalloc/cudaFree,
+ * code that cannot create a handle since lattice_setup allocates).  The paper has no counterpart
+ * of this entry point.  Same arguments and results as greedy_select for
  * T, n_rows, n_cols, eps, max_nr, S, n_r, alpha, with no handle: the work runs on cuda_stream
  * (NULL = legacy default stream).  All workspace lives in one file-scope device array of
  * 16 MiB (2 Mi doubles) that every device loading the library holds until process exit; it
@@ -216,6 +216,22 @@ typedef struct {
                               one dense product per solve; FP32 copy in the mixed modes), -1
                               (default) block LU when the explicit inverse would hold more than
                               8192^2 entries (N blocks of size m, N m > 8192) */
+  int32_t precond_tangent; /* principal tangents the preconditioner's local blocks are built from:
+                              0 the full tangent K^r (Section 3.1.4), 1 its material part (the
+                              geometric stress term delta_ij sigma_kl of D dropped: positive
+                              definite local blocks whatever the prestress), -1 (default) 1 in 3D,
+                              0 in 2D.  The Krylov operator always uses the full reduced tangent,
+                              so the choice changes iteration counts, not the solution */
+  int32_t min_enrich;      /* primal enrichment level to start from (0 = corners only); the
+                              level only grows (Section 3.3.2) */
+  int32_t inner_its;       /* mixed modes: > 0 makes FGMRES's preconditioner an inner flexible
+                              GMRES of at most inner_its iterations on the same saddle-point
+                              system with the FP32 reduced tangent action as its operator and the
+                              block preconditioner of Eq. (ifetidp_precond) as its preconditioner;
+                              the outer FGMRES keeps the FP64 operator, so the solution is that of
+                              the FP64 reduced tangent.  0: the block preconditioner directly.
+                              Ignored in LAT_FP64 */
+  double inner_rtol;       /* inner GMRES stops early at this relative residual */
 } lat_newton_opts;
 
 typedef struct {
@@ -229,11 +245,15 @@ typedef struct {
   double t_residual_ms, t_select_ms, t_setup_ms, t_krylov_ms, t_linesearch_ms; /* phase times */
   int32_t pcg_its_total;   /* interface PCG iterations inside the preconditioner */
   int32_t enrich_level;    /* primal enrichment level in use at exit */
+  int32_t inner_its_total; /* inner FP32-operator GMRES iterations (mixed modes, inner_its > 0) */
 } lat_newton_report;
 
 /* Default options (eps 3e-4 in 2D and 5e-3 in 3D, max_nr 256, newton_rtol 1e-8, krylov_rtol
  * 1e-10 for FP64 and 1e-6 for the mixed modes, restart 60, interface PCG to 3e-2 with at most 100
- * iterations, Armijo cap 30, Dirichlet interface preconditioner, enrichment up to level 3). */
+ * iterations, Armijo cap 30, Dirichlet interface preconditioner, enrichment up to level 3,
+ * preconditioner from the full tangent in 2D and from its material part in 3D, starting
+ * enrichment level 0; in the mixed modes an inner FP32-operator GMRES of at most 20 iterations
+ * to 1e-2 as FGMRES's preconditioner). */
 lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 
 /* Newton-Raphson for one load step (Section 2.2.5) from the initial guess in u_glob (dev,
@@ -276,13 +296,16 @@ lat_status feti_to_global(lat_handle h, const double* v, double* u_glob);
 lat_status feti_from_global(lat_handle h, const double* u_glob, double* v);
 
 /* Kernel timing: while enabled, CUDA events are recorded on the handle's stream around every
- * launch of the named kernels ("residual", "tangent_full", "tangent_reduced", "greedy_update",
- * "apply_reduced", "apply_percell", "local_segmm", "local_gemv", "local_tc" and their "_dual" /
- * "_dual_in" variants inside the interface solve, "gj_update", "gj_pivot", "densify",
- * "phi_schur", "coarse_blocked", "coarse_gemv", "krylov_orth").  While enabled, the interface
- * PCG iteration runs launch by launch instead of as a CUDA-graph replay, so that every launch
- * is timed.  lattice_set_timing clears the records; lattice_kernel_time returns the summed
- * duration (host ms) and the launch count of one name since then. */
+ * launch of the named kernels ("residual", "tangent_full", "tangent_material",
+ * "tangent_reduced", "greedy_update", "apply_reduced" / "apply_reduced_fp32", "apply_percell" /
+ * "apply_percell_fp32", "local_segmm", "local_gemv", "local_tc" and their "_dual" / "_dual_in"
+ * variants inside the interface solve, "dual_schur" / "dual_schur_tc", "gj_update", "gj_pivot", "densify",
+ * "phi_schur", "coarse_blocked", "coarse_gemv", "coarse_solve", "krylov_orth").  enable = 1
+ * times every named kernel; the interface PCG iteration then runs launch by launch instead of
+ * as a CUDA-graph replay, so that every launch is timed.  enable = 2 times only the tangent
+ * action kernels ("apply_*") and keeps the graph replays.  lattice_set_timing clears the
+ * records; lattice_kernel_time returns the summed duration (host ms) and the launch count of
+ * one name since then. */
 lat_status lattice_set_timing(lat_handle h, int32_t enable);
 lat_status lattice_kernel_time(lat_handle h, const char* name, double* total_ms, int32_t* launches);
 

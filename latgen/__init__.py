@@ -219,7 +219,8 @@ def make_case(which: str) -> LoadCase:
     strut10    3D, 10^3 strut cells, -15 % in 15 steps
     strut20    3D, 20^3 strut cells, theta ~ U[0.9,1.1] (seed 4), -20 % in 20 steps
     strut5     3D, 5^3 strut cells, -15 % in 15 steps (small 3D case)
-    ring2 / strut2  tiny lattices for tests
+    strut222   3D, 2^3 strut cells of the same 12^3-voxel cell, -15 % in 15 steps (3D parity case)
+    ring2 / strut2  tiny lattices for tests (strut2: a coarser 6^3-voxel cell)
     """
     table = {
         "ring4": (ring_cell, (8,), (4, 4), None, 0.10, 10, 3e-4),
@@ -229,6 +230,7 @@ def make_case(which: str) -> LoadCase:
         "strut10": (strut_cell, (12, 0.15), (10, 10, 10), None, 0.15, 15, 5e-3),
         "strut20": (strut_cell, (12, 0.15), (20, 20, 20), 4, 0.20, 20, 5e-3),
         "strut5": (strut_cell, (12, 0.15), (5, 5, 5), None, 0.15, 15, 5e-3),
+        "strut222": (strut_cell, (12, 0.15), (2, 2, 2), None, 0.15, 15, 5e-3),
         "strut2": (strut_cell, (6, 0.2), (2, 2, 2), 3, 0.05, 2, 5e-3),
     }
     if which not in table:

@@ -43,12 +43,22 @@ class Problem:
         self.free = np.nonzero(~fixed)[0]
         self.top_axis_dofs = top * d + lat.load_axis
         self.bot_dofs = np.concatenate([bot * d + i for i in range(d)])
-        self._pattern_coo()
+        self._coo = None
 
     def _pattern_coo(self):
-        cd = self.cell_dofs
-        self.K_rows = cd[:, self.cell.rows].ravel()
-        self.K_cols = cd[:, self.cell.cols].ravel()
+        # global (row, col) of every local tangent entry, built on first use (N_s x nnz each)
+        if self._coo is None:
+            cd = self.cell_dofs
+            self._coo = (cd[:, self.cell.rows].ravel(), cd[:, self.cell.cols].ravel())
+        return self._coo
+
+    @property
+    def K_rows(self):
+        return self._pattern_coo()[0]
+
+    @property
+    def K_cols(self):
+        return self._pattern_coo()[1]
 
     def dirichlet_values(self, step):
         """Prescribed global displacement values at fixed DOFs for load step ``step``."""

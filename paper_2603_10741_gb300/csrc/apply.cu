@@ -275,35 +275,43 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-template <int GR, bool PAIR>
+// Grid: x = node group, y = cell tile, so that the groups of one tile run close together and
+// find its x rows in L2.  (64-cell tiles, two cells per lane, half the shared memory per CTA,
+// were measured slower for every N_r on 8000 strut cells.)
+template <int GR, bool PAIR, int TW>
 __global__ void __launch_bounds__(GR * 32)
     k_apply_groups(int n_cells, const int* __restrict__ grp_rows, const int* __restrict__ grp_ucptr,
                    const int* __restrict__ grp_ucol, const int* __restrict__ grp_pp, const int* __restrict__ pair_u,
                    int64_t n_pairs, int n_r, int rch, const float* __restrict__ Kg, const float* __restrict__ alpha,
                    const float* __restrict__ X, float* __restrict__ Y) {
+  constexpr int CPL = TW / 32;
+  static_assert(CPL == 4, "four cells per lane: 16-byte rows");
   extern __shared__ __align__(16) float smf[];
-  const int g = blockIdx.y;
+  const int g = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile0 = blockIdx.x * 128;
-  const int nct = min(128, n_cells - tile0);                 // a multiple of 4
+  const int tile0 = blockIdx.y * TW;
+  const int nct = min(TW, n_cells - tile0);                  // a multiple of 4
   const int u0 = grp_ucptr[g], nu = grp_ucptr[g + 1] - u0;
   const int gp0 = grp_pp[g * (GR + 1)], np = grp_pp[g * (GR + 1) + GR] - gp0;
-  float* xs = smf;                                           // [nu * 3][128]
-  float* ks = smf + (size_t)nu * 3 * 128;                    // [rch][np][12]
+  float* xs = smf;                                           // [nu * 3][TW]
+  float* ks = smf + (size_t)nu * 3 * TW;                     // [rch][np][12]
+  const bool live = lane * CPL < nct;
   for (int t = warp; t < nu * 3; t += GR) {
     const int b = grp_ucol[u0 + t / 3], j = t % 3;
-    float* dst = xs + (size_t)t * 128 + lane * 4;
-    if (lane * 4 < nct) cp_async16(dst, X + (size_t)(b * 3 + j) * n_cells + tile0 + lane * 4);
+    float* dst = xs + (size_t)t * TW + lane * CPL;
+    const float* src = X + (size_t)(b * 3 + j) * n_cells + tile0 + lane * CPL;
+    if (live) cp_async16(dst, src);
     else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   const int a = grp_rows[g * GR + warp];
   const int q0 = grp_pp[g * (GR + 1) + warp] - gp0, nq = grp_pp[g * (GR + 1) + warp + 1] - gp0 - q0;
   const int myu = lane < nq ? pair_u[gp0 + q0 + lane] : 0;  // nq <= 27
-  const bool live = lane * 4 < nct;
-  const int c = live ? tile0 + lane * 4 : 0;
-  float2 y[3][2];
+  const int c = live ? tile0 + lane * CPL : 0;
+  float2 y[3][CPL / 2];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) y[i][0] = y[i][1] = make_float2(0.f, 0.f);
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int h = 0; h < CPL / 2; ++h) y[i][h] = make_float2(0.f, 0.f);
   for (int r0 = 0; r0 < n_r; r0 += rch) {
     const int nr = min(rch, n_r - r0);
     if (r0 > 0) __syncthreads();                             // the previous chunk is consumed
@@ -315,16 +323,23 @@ __global__ void __launch_bounds__(GR * 32)
     __syncthreads();
     if (a < 0) continue;                                     // warp-uniform
     for (int rr = 0; rr < nr; ++rr) {
-      float2 z[3][2];
+      float2 z[3][CPL / 2];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) z[i][0] = z[i][1] = make_float2(0.f, 0.f);
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int h = 0; h < CPL / 2; ++h) z[i][h] = make_float2(0.f, 0.f);
       const float* kq = ks + ((size_t)rr * np + q0) * 12;
 #pragma unroll 4
       for (int i = 0; i < nq; ++i) {
         const int u = __shfl_sync(0xffffffffu, myu, i);
-        float4 x[3];
+        float2 x[3][CPL / 2];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) x[j] = *reinterpret_cast<const float4*>(xs + (size_t)(u * 3 + j) * 128 + lane * 4);
+        for (int j = 0; j < 3; ++j) {
+          const float* xr = xs + (size_t)(u * 3 + j) * TW + lane * CPL;
+          const float4 v = *reinterpret_cast<const float4*>(xr);
+          x[j][0] = make_float2(v.x, v.y);
+          x[j][1] = make_float2(v.z, v.w);
+        }
         float k[12];
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
@@ -336,30 +351,35 @@ __global__ void __launch_bounds__(GR * 32)
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             const float kv = k[ii * 3 + j];
-            if (PAIR) {
-              const float2 kk = make_float2(kv, kv);
-              z[ii][0] = __ffma2_rn(kk, make_float2(x[j].x, x[j].y), z[ii][0]);
-              z[ii][1] = __ffma2_rn(kk, make_float2(x[j].z, x[j].w), z[ii][1]);
-            } else {
-              z[ii][0].x = fmaf(kv, x[j].x, z[ii][0].x);
-              z[ii][0].y = fmaf(kv, x[j].y, z[ii][0].y);
-              z[ii][1].x = fmaf(kv, x[j].z, z[ii][1].x);
-              z[ii][1].y = fmaf(kv, x[j].w, z[ii][1].y);
+#pragma unroll
+            for (int h = 0; h < CPL / 2; ++h) {
+              if (PAIR) {
+                z[ii][h] = __ffma2_rn(make_float2(kv, kv), x[j][h], z[ii][h]);
+              } else {
+                z[ii][h].x = fmaf(kv, x[j][h].x, z[ii][h].x);
+                z[ii][h].y = fmaf(kv, x[j][h].y, z[ii][h].y);
+              }
             }
           }
       }
-      const float4 al = __ldg(reinterpret_cast<const float4*>(alpha + (size_t)(r0 + rr) * n_cells + c));
-#pragma unroll
-      for (int ii = 0; ii < 3; ++ii) {
-        y[ii][0] = __ffma2_rn(make_float2(al.x, al.y), z[ii][0], y[ii][0]);
-        y[ii][1] = __ffma2_rn(make_float2(al.z, al.w), z[ii][1], y[ii][1]);
+      float2 al[CPL / 2];
+      {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(alpha + (size_t)(r0 + rr) * n_cells + c));
+        al[0] = make_float2(v.x, v.y);
+        al[1] = make_float2(v.z, v.w);
       }
+#pragma unroll
+      for (int ii = 0; ii < 3; ++ii)
+#pragma unroll
+        for (int h = 0; h < CPL / 2; ++h) y[ii][h] = __ffma2_rn(al[h], z[ii][h], y[ii][h]);
     }
   }
   if (a < 0 || !live) return;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    *reinterpret_cast<float4*>(Y + (size_t)(a * 3 + i) * n_cells + c) = make_float4(y[i][0].x, y[i][0].y, y[i][1].x, y[i][1].y);
+  for (int i = 0; i < 3; ++i) {
+    float* yr = Y + (size_t)(a * 3 + i) * n_cells + c;
+    *reinterpret_cast<float4*>(yr) = make_float4(y[i][0].x, y[i][0].y, y[i][1].x, y[i][1].y);
+  }
 }
 
 // principal blocks [n_r][n_blk][9] -> group order [n_r][n_blk][12] (zero padded, 16-byte rows)
@@ -413,10 +433,12 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
   if (h->force_all) {
     dim3 blk(32, 8);
     dim3 grid(div_up(h->n_cells, 32), div_up(h->n_nodes_cell, 8));
-    KernelTimer kt(h, "apply_percell");
+    KernelTimer kt(h, sizeof(T) == 4 ? "apply_percell_fp32" : "apply_percell");
     LAT_LAUNCH(h, k_apply_percell<T, D, FETI><<<grid, blk, 0, h->stream>>>(A, Kp, X, Y));
-  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0 && group_plan(h, &gp)) {
-    // 3D FP32: node groups staged in shared memory
+  } else if (D == 3 && sizeof(T) == 4 && !FETI && h->n_cells % 4 == 0 &&
+             ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0 && group_plan(h, &gp)) {
+    // 3D FP32: node groups staged in shared memory (16-byte copies of X rows and 16-byte stores
+    // of Y rows: taken only for 16-byte aligned vectors, the per-(cell, node) kernel otherwise)
     const lat_ctx::NodeGroups& G = *gp.G;
     const int rch = gp.rch;
     const size_t shm = gp.shm;
@@ -429,24 +451,20 @@ void launch(lat_ctx* h, const ApplyArgs& A, const T* Kp, const T* alpha, const T
       h->kg_version = h->sel_version;
       h->kg_gr = G.GR;
     }
-    const dim3 grid((unsigned)tiles, G.n_grp);
+    const dim3 grid(G.n_grp, (unsigned)tiles);
     const float* al = reinterpret_cast<const float*>(alpha);
     const float* xx = reinterpret_cast<const float*>(X);
     float* yy = reinterpret_cast<float*>(Y);
-    KernelTimer kt(h, "apply_reduced");
-    if (G.GR == 16) {
-      LAT_CUDA(cudaFuncSetAttribute(k_apply_groups<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_apply_groups<16, false><<<grid, 16 * 32, shm, h->stream>>>(
-                        h->n_cells, G.rows.p, G.ucptr.p, G.ucol.p, G.pp.p, G.pair_u.p, nblk, h->n_r, rch, h->Kg.p,
-                        al, xx, yy));
-    } else {
-      LAT_CUDA(cudaFuncSetAttribute(k_apply_groups<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_apply_groups<8, true><<<grid, 8 * 32, shm, h->stream>>>(
-                        h->n_cells, G.rows.p, G.ucptr.p, G.ucol.p, G.pp.p, G.pair_u.p, nblk, h->n_r, rch, h->Kg.p,
-                        al, xx, yy));
-    }
+    KernelTimer kt(h, "apply_reduced_fp32");
+    auto go = [&](auto kern, int threads) {
+      LAT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+      LAT_LAUNCH(h, kern<<<grid, threads, shm, h->stream>>>(h->n_cells, G.rows.p, G.ucptr.p, G.ucol.p, G.pp.p,
+                                                           G.pair_u.p, nblk, h->n_r, rch, h->Kg.p, al, xx, yy));
+    };
+    if (G.GR == 16) go(k_apply_groups<16, false, 128>, 16 * 32);
+    else go(k_apply_groups<8, true, 128>, 8 * 32);
   } else {
-    KernelTimer kt(h, "apply_reduced");
+    KernelTimer kt(h, sizeof(T) == 4 ? "apply_reduced_fp32" : "apply_reduced");
     if (D == 3 && sizeof(T) == 4) {
       // FP32 in 3D: a thread per (cell, node) with the alpha-combined block formed in registers
       // needs no staging and keeps more warps in flight; the staged form's 81 neighbour values

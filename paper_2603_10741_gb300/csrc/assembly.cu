@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kCellThreads)
     k_tangent(int nn, GeomArgs g, ColorTable ct, const int* __restrict__ cell_nodes,
               const int* __restrict__ cells, const int* __restrict__ elem_blk,
               const double* __restrict__ mu_cell, double lam, const double* __restrict__ u_glob,
-              int64_t nnz, double* __restrict__ K_out, double* __restrict__ minJ_out) {
+              int64_t nnz, double* __restrict__ K_out, double* __restrict__ minJ_out, int geo) {
   constexpr int NEN = 1 << D;
   extern __shared__ double sm[];
   double* u_loc = sm;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(kCellThreads)
         }
 #pragma unroll
         for (int b = 0; b < NEN; ++b) {
-          double gb[D], hb[D], gab = 0;
+          double gb[D], hb[D], gab = 0, hab = 0;
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             gb[k] = gq[b * D + k];
@@ -202,12 +202,17 @@ __global__ void __launch_bounds__(kCellThreads)
 #pragma unroll
             for (int k = 0; k < D; ++k) v += Fi[k][i] * gb[k];
             hb[i] = v;
+            hab += ha[i] * v;
           }
+          // diagonal term: mu g_a.g_b holds the geometric part delta_ij J h_a^T sigma h_b =
+          // mu (g_a.g_b - h_a.h_b) + lam ln J h_a.h_b; without it (geo = 0) what remains is the
+          // material part, the contraction of C_ikjl alone: (mu - lam ln J) h_a.h_b
+          const double dg = geo ? cm * gab : cg * hab;
 #pragma unroll
           for (int i = 0; i < D; ++i)
 #pragma unroll
             for (int j = 0; j < D; ++j)
-              acc[b][i][j] += (i == j ? cm * gab : 0.0) + cl * ha[i] * hb[j] + cg * hb[i] * ha[j];
+              acc[b][i][j] += (i == j ? dg : 0.0) + cl * ha[i] * hb[j] + cg * hb[i] * ha[j];
         }
       }
       const int* eb = elem_blk + (e * NEN + a) * NEN;
@@ -445,21 +450,21 @@ void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_g
 }
 
 void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, int n_sel,
-                 double* K_out, bool* negJ) {
+                 double* K_out, bool* negJ, bool geometric) {
   if (n_sel <= 0) return;
   LAT_CUDA(cudaMemsetAsync(K_out, 0, (size_t)n_sel * h->nnz * sizeof(double), h->stream));
   const size_t shm = (size_t)h->n_loc * sizeof(double);
   h->minJ_cell.ensure(std::max(h->n_cells, n_sel));
   auto g = geom(h, quad);
   auto ct = colors(h);
-  KernelTimer kt(h, quad ? "tangent_reduced" : "tangent_full");
+  KernelTimer kt(h, quad ? "tangent_reduced" : (geometric ? "tangent_full" : "tangent_material"));
   if (h->dim == 2) {
     LAT_LAUNCH(h, k_tangent<2><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
-        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p));
+        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p, geometric ? 1 : 0));
   } else {
     LAT_CUDA(cudaFuncSetAttribute(k_tangent<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
     LAT_LAUNCH(h, k_tangent<3><<<n_sel, kCellThreads, shm, h->stream>>>(h->n_nodes_cell, g, ct, h->cell_nodes.p,
-        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p));
+        cells, h->elem_blk.p, h->mu_cell.p, h->lam, u_glob, h->nnz, K_out, h->minJ_cell.p, geometric ? 1 : 0));
   }
   LAT_CHECK_LAUNCH();
   if (negJ) {

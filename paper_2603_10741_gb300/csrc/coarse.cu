@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(256)
     }
     rs[(size_t)b * Rp + lr] = v;
   }
-  __syncthreads();
+  // every CTA of the cluster must be running before a peer's shared memory is written
+  cl.sync();
   {
     const int b = FWD ? 0 : N - 1;
     for (int t = threadIdx.x; t < nr * C; t += blockDim.x) {

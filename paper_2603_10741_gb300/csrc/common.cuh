@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <cstdio>
 #include <map>
 #include <string>
@@ -148,6 +149,7 @@ struct lat_ctx {
   DBuf<float> alpha32;
   DBuf<double> Kp;                    // [n_r][nnz]
   DBuf<float> Kp32;
+  DBuf<double> Kp_mat;                // [n_r][nnz] material part of K^r (preconditioner option)
   // 3D FP32 reduced action: the cell's nodes in groups of GR = 8 and 16 (one CTA each), with the
   // union of each group's neighbour nodes and its node blocks in group order (built at setup)
   struct NodeGroups {
@@ -180,9 +182,10 @@ struct lat_ctx {
   DBuf<float> SDD32;
   DBuf<double> gj_P, gj_C, gj_R;      // Gauss-Jordan workspace (pivot inverse, column and row panels)
   DBuf<int> class_rep_d;
-  DBuf<__nv_bfloat16> G16[3], Xb16;    // BF16 local matrices (one view per KinvMode), packed cell vectors
-  int g16_ld[3] = {0, 0, 0};           // their row strides
-  int64_t g16_lo[3] = {0, 0, 0};       // offset of the low BF16 part after the high part
+  DBuf<__nv_bfloat16> G16[4], Xb16;    // BF16 local matrices (one view per KinvMode, then the dual
+                                       // Schur complements S_DD), packed cell vectors
+  int g16_ld[4] = {0, 0, 0, 0};        // their row strides
+  int64_t g16_lo[4] = {0, 0, 0, 0};    // offset of the low BF16 part after the high part
   DBuf<double> KRP, Coarse, CoarseInv;
   DBuf<float> CoarseInv32;             // FP32 copy of the coarse inverse (mixed modes)
   int64_t coarse32_ld = 0;             // its row stride (a multiple of 4)
@@ -191,6 +194,9 @@ struct lat_ctx {
   DBuf<double> kv_tmp[6];             // saddle-point sized temporaries
   DBuf<double> pcg_ws;                // interface PCG vectors (5 x n_lambda)
   DBuf<double> V, Zk, Hh, gmres_small, dots_part;
+  DBuf<double> kscal[2];              // FGMRES device scalars of the outer and the inner level
+  DBuf<double> V2, Z2, Hh2, gmres_small2;   // inner FGMRES (FP32 operator) of the mixed modes
+  int64_t inner_its_total = 0;        // inner FGMRES iterations since the last reset
   DBuf<int> flag;
   DBuf<double> red_part;            // reduction scratch
   int max_tiles = 0;
@@ -205,6 +211,7 @@ struct lat_ctx {
   // optional per-kernel timing: CUDA events recorded on the launching stream around the
   // launches of named kernels (lattice_set_timing / lattice_kernel_time)
   bool timing = false;
+  bool timing_apply_only = false;       // time only the reduced / plain tangent action kernels
   // interface PCG iteration captured as a CUDA graph (dropped whenever the solver is set up)
   cudaGraphExec_t pcg_exec = nullptr;
   cudaStream_t cap_stream = nullptr;    // private stream the graph is captured on
@@ -232,6 +239,7 @@ struct KernelTimer {
   }
   KernelTimer(lat_ctx* h_, const char* n) : h(h_), name(n) {
     if (!h->timing) return;
+    if (h->timing_apply_only && std::strncmp(n, "apply_", 6) != 0) return;
     a = take(h);
     b = take(h);
     cudaEventRecord(a, h->stream);
@@ -353,7 +361,7 @@ __device__ __forceinline__ T block_max(T v, T* sh) {
 void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_glob,
                   double* min_detF_host, bool* negJ);
 void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, int n_sel,
-                 double* K_out, bool* negJ);
+                 double* K_out, bool* negJ, bool geometric = true);
 void run_tangent_apply_exact(lat_ctx* h, const double* u_glob, const double* v_glob,
                              double* y_glob);
 void run_grad_mu(lat_ctx* h, const double* u_glob, const double* w_glob, double* grad);
@@ -365,7 +373,7 @@ void run_greedy(lat_ctx* h, const double* T, int64_t n_rows, int n_cols, double 
                 double* max_res_host);
 void run_apply(lat_ctx* h, const void* x, void* y, int dtype, const double* xP, bool feti);
 void build_node_groups(lat_ctx* h);
-void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o);
+void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_glob);
 // square tile (64, 32 or 16) for batched FP64 products over n x n matrices: the least padded
 // work per busy SM (padding of n to the tile, and the share of the SMs the tiles occupy)
 inline int fp64_tile(int n, int64_t batch, int n_sm) {
@@ -400,7 +408,7 @@ void run_mask(lat_ctx* h, const double* x, double* y, int keep_fixed);
 void run_adjoint_w(lat_ctx* h, const double* lam, const double* u, double* w);
 void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool force_all);
 void build_feti(lat_ctx* h, int level);
-void prepare_enriched(lat_ctx* h, const lat_newton_opts* o);
+void prepare_enriched(lat_ctx* h, const lat_newton_opts* o, const double* u_glob);
 void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit, int split = -1,
                double* snap = nullptr);
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
@@ -411,3 +419,4 @@ void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)
 enum KinvMode { KINV_FULL = 0, KINV_DUAL = 1, KINV_DUAL_IN = 2 };
 void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode);
+void run_sdd_tc(lat_ctx* h, const double* X, double* Y);

@@ -549,6 +549,44 @@ __global__ void k_coarse(int64_t n_ent, int64_t n_primal, int n_P, const int* __
 }
 
 
+// saddle-point local part -> plain FP32 cell-stacked vector for the FP32 action: corner rows from
+// the primal part through pidx (0 for a Dirichlet primal DOF), other rows copied, Dirichlet rows 0
+// (the operand the FETI-mode action kernels form on the fly)
+__global__ void k_feti_pack32(int n_cells, int D, int n_P, const int* __restrict__ corner_of_node,
+                              const int* __restrict__ pidx, const uint8_t* __restrict__ fixed,
+                              const double* __restrict__ v, const double* __restrict__ xP, float* __restrict__ x) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (s >= n_cells) return;
+  const int c = corner_of_node[a];
+  for (int i = 0; i < D; ++i) {
+    const size_t e = (size_t)(a * D + i) * n_cells + s;
+    double val;
+    if (c >= 0) {
+      const int p = pidx[(size_t)s * n_P + c * D + i];
+      val = p >= 0 ? xP[p] : 0.0;
+    } else {
+      val = fixed[e] ? 0.0 : v[e];
+    }
+    x[e] = (float)val;
+  }
+}
+
+// FP32 action result -> saddle-point local part (FP64): Dirichlet rows of non-corner DOFs 0,
+// corner rows kept for the primal assembly that follows
+__global__ void k_feti_unpack64(int n_cells, int D, const int* __restrict__ corner_of_node,
+                                const uint8_t* __restrict__ fixed, const float* __restrict__ y,
+                                double* __restrict__ w) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = blockIdx.y;
+  if (s >= n_cells) return;
+  const bool corner = corner_of_node[a] >= 0;
+  for (int i = 0; i < D; ++i) {
+    const size_t e = (size_t)(a * D + i) * n_cells + s;
+    w[e] = (!corner && fixed[e]) ? 0.0 : (double)y[e];
+  }
+}
+
 __global__ void k_d2f(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (float)x[i];
@@ -594,8 +632,10 @@ __global__ void __launch_bounds__(256)
   const int rows = n_Kr + n_P;
   const TG* g = G + (size_t)slot[s] * kstride;
   const double inv = 1.0 / cscale[s];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < rows; i += nw) {
+  // the cell's rows are shared by the gridDim.y CTAs of the cell (several when cells are few)
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int wid = blockIdx.y * nw + (threadIdx.x >> 5), nwt = gridDim.y * nw;
+  for (int i = wid; i < rows; i += nwt) {
     const TG* gi = g + (size_t)i * ldg;
     double v = 0;
     for (int k = lane; k < n_Kc; k += 32) v += (double)gi[k] * xs[k];
@@ -743,8 +783,9 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   const TS* S = SDD + (size_t)slot[s] * n_D * n_D;
   const double c = cscale[s];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = wid; i < n_D; i += nw) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int wid = blockIdx.y * nw + (threadIdx.x >> 5), nwt = gridDim.y * nw;
+  for (int i = wid; i < n_D; i += nwt) {
     const TS* si = S + (size_t)i * n_D;
     TS v = 0;
     for (int k = lane; k < n_D; k += 32) v = fma(si[k], xs[k], v);
@@ -900,6 +941,13 @@ __global__ void k_gmres_solve(int k, int m, const double* __restrict__ H, const 
   }
 }
 
+// CTAs per cell of the warp-per-row local products: one while the cells fill the GPU, more for
+// small lattices (at least 64 rows per CTA) so that a handful of cells still reaches every SM
+int split_rows(const lat_ctx* h, int n_cells, int rows) {
+  const int want = (int)div_up(2 * h->n_sm, std::max(1, n_cells));
+  return std::max(1, std::min(want, (int)div_up(rows, 64)));
+}
+
 // cells per segmented-GEMM tile: 4 in FP64, 64 in the mixed modes
 int seg_bn(lat_ctx* h) { return h->prec == LAT_FP64 ? 4 : 64; }
 
@@ -976,9 +1024,24 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
 namespace {
 }  // namespace
 
-void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
-  (void)o;
+// principal tangents the local blocks are built from: the full K^r, or its material part
+// evaluated at u_glob for the same principal cells (precond_tangent, Section 3.1.4)
+bool precond_material(const lat_ctx* h, const lat_newton_opts* o) {
+  const int pt = o ? o->precond_tangent : -1;
+  return pt == 1 || (pt < 0 && h->dim == 3);
+}
+
+void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_glob) {
   LAT_REQUIRE(h->n_r > 0, LAT_EINVAL, "select principal cells first");
+  const double* Kpre = h->Kp.p;
+  if (precond_material(h, o)) {
+    LAT_REQUIRE(u_glob, LAT_EINVAL, "the material-part preconditioner needs the state");
+    h->Kp_mat.ensure((size_t)h->n_r * h->nnz);
+    bool neg = false;
+    run_tangent(h, u_glob, 0, h->force_all ? nullptr : h->S.p, h->n_r, h->Kp_mat.p, &neg, false);
+    LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 in a principal tangent");
+    Kpre = h->Kp_mat.p;
+  }
   drop_pcg_graph(h);   // buffers and sizes below may change
   const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
   h->flag.ensure(4);
@@ -1040,11 +1103,11 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o) {
     dim3 grid(div_up(h->n_nodes_cell, 128), nk);
     if (h->dim == 2)
       LAT_LAUNCH(h, k_densify<2><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
-          h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
+          h->blk_ptr.p, h->blk_col.p, h->nnz, Kpre, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
           nR, nP, h->G.p, h->KRP.p, h->Sloc.p));
     else
       LAT_LAUNCH(h, k_densify<3><<<grid, 128, 0, h->stream>>>(nk, h->key_list.p, h->n_classes, crep.p, ns, h->n_nodes_cell,
-          h->blk_ptr.p, h->blk_col.p, h->nnz, h->Kp.p, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
+          h->blk_ptr.p, h->blk_col.p, h->nnz, Kpre, h->rpos.p, h->corner_of_node.p, h->loc_fixed.p,
           nR, nP, h->G.p, h->KRP.p, h->Sloc.p));
     LAT_CHECK_LAUNCH();
   }
@@ -1124,11 +1187,28 @@ const double* pr_of(lat_ctx* h, const double* v) { return v + (size_t)h->n_loc *
 const double* la_of(lat_ctx* h, const double* v) { return v + (size_t)h->n_loc * h->n_cells + h->n_primal; }
 
 // w_u = K~ v_u (+ B^T v_l when with_bt), w_l = B v_u  (saddle-point operator)
-void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda) {
+// op32: the reduced tangent action in FP32 (the operator of the mixed modes' inner GMRES).  The
+// partially assembled vector goes to a plain FP32 cell-stacked vector (corner rows gathered from
+// the primal part, Dirichlet rows zero), the FP32 copies of K^r and alpha act on it with the
+// plain (non-FETI) action kernels, and the result comes back to FP64 with the Dirichlet rows of
+// non-corner DOFs cleared; index work (primal assembly, jumps) is the same.  The outer FGMRES
+// always takes the FP64 action, so the system it solves to its tolerance is the FP64 one.
+void feti_operator(lat_ctx* h, const double* v, double* w, bool with_lambda, bool op32 = false) {
   const double* vP = pr_of(h, v);
-  // the Krylov operator stays FP64 in every mode: FGMRES then solves the FP64 system to its
-  // tolerance, while the mixed modes lower the precision of the preconditioner only
-  run_apply(h, v, w, 0, vP, true);
+  if (op32) {
+    const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
+    h->x32.ensure(nloc);
+    h->y32.ensure(nloc);
+    const dim3 grid(div_up(h->n_cells, 256), h->n_nodes_cell);
+    LAT_LAUNCH(h, k_feti_pack32<<<grid, 256, 0, h->stream>>>(h->n_cells, h->dim, h->n_P, h->corner_of_node.p,
+        h->pidx.p, h->loc_fixed.p, v, vP, h->x32.p));
+    run_apply(h, h->x32.p, h->y32.p, 1, nullptr, false);
+    LAT_LAUNCH(h, k_feti_unpack64<<<grid, 256, 0, h->stream>>>(h->n_cells, h->dim, h->corner_of_node.p,
+        h->loc_fixed.p, h->y32.p, w));
+    LAT_CHECK_LAUNCH();
+  } else {
+    run_apply(h, v, w, 0, vP, true);
+  }
   // primal rows -> assembled primal part, then clear corner rows
   if (h->n_primal)
     LAT_LAUNCH(h, k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
@@ -1196,11 +1276,11 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
     const size_t shm = (size_t)nKc * sizeof(double);
     if (lo) {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_local_gemv<float><<<ns, 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G32.p + off,
+      LAT_LAUNCH(h, k_local_gemv<float><<<dim3(ns, split_rows(h, ns, nKr + nP)), 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G32.p + off,
           h->key_slot.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     } else {
       LAT_CUDA(cudaFuncSetAttribute(k_local_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_local_gemv<double><<<ns, 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G.p + off,
+      LAT_LAUNCH(h, k_local_gemv<double><<<dim3(ns, split_rows(h, ns, nKr + nP)), 256, shm, h->stream>>>(ns, nKr, nKc, nP, nR, kstride, h->G.p + off,
           h->key_slot.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     }
   } else if (h->prec == LAT_MIXED_BF16) {
@@ -1257,7 +1337,9 @@ void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2
     const int nD = h->n_R - h->n_I;
     const size_t shm = (size_t)nD * sizeof(double);
     const bool seg = (int64_t)h->n_keys * 8 <= h->n_cells;
-    if (seg) {
+    if (seg && h->prec == LAT_MIXED_BF16) {
+      run_sdd_tc(h, t1, t2);   // tcgen05, BF16 operand pairs, FP32 accumulation
+    } else if (seg) {
       KernelTimer kt(h, "dual_schur");
       const int* rd = h->rdofs.p + h->n_I;
       dim3 grid(h->max_tiles, div_up(nD, 64));
@@ -1270,11 +1352,11 @@ void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2
             rd, h->pdofs.p, t1, t2));
     } else if (h->prec == LAT_FP64) {
       LAT_CUDA(cudaFuncSetAttribute(k_dual_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_dual_schur<double><<<h->n_cells, 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD.p,
+      LAT_LAUNCH(h, k_dual_schur<double><<<dim3(h->n_cells, split_rows(h, h->n_cells, nD)), 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD.p,
           h->key_slot.p, h->c_cell.p, h->rdofs.p, t1, t2));
     } else {
       LAT_CUDA(cudaFuncSetAttribute(k_dual_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
-      LAT_LAUNCH(h, k_dual_schur<float><<<h->n_cells, 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD32.p,
+      LAT_LAUNCH(h, k_dual_schur<float><<<dim3(h->n_cells, split_rows(h, h->n_cells, nD)), 256, shm, h->stream>>>(h->n_cells, h->n_I, nD, h->SDD32.p,
           h->key_slot.p, h->c_cell.p, h->rdofs.p, t1, t2));
     }
   } else if (h->prec == LAT_FP64) {
@@ -1362,7 +1444,7 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
         LAT_CUDA(cudaMemcpyAsync(h->h_pinned + 8, sc, 6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LAT_CHECK_LAUNCH();
     };
-    bool graph = !h->timing && h->graphs_ok;
+    bool graph = (!h->timing || h->timing_apply_only) && h->graphs_ok;
     if (graph && (!h->pcg_exec || h->pcg_exec_check != (int)check)) {
       if (h->pcg_exec) {
         cudaGraphExecDestroy(h->pcg_exec);
@@ -1425,29 +1507,46 @@ void run_block_precond(lat_ctx* h, const double* v, double* w, int pcg_iters, do
   LAT_CHECK_LAUNCH();
 }
 
-// right-preconditioned restarted FGMRES from x (in/out); returns iterations, *rel = final estimate
-int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o, double* rel_out) {
+namespace {
+
+// one FGMRES level: its Krylov basis V, preconditioned vectors Z, Hessenberg matrix, Givens
+// data, device scalars and the operator output vector
+struct GmresLevel {
+  DBuf<double>* V;
+  DBuf<double>* Z;
+  DBuf<double>* H;
+  DBuf<double>* small;
+  DBuf<double>* scal;
+  double* w;
+};
+
+// right-preconditioned restarted FGMRES from x (in/out, or zero when x_zero); returns iterations,
+// *rel = final estimate.  op32 selects the FP32 reduced tangent action as the operator.
+template <typename Prec>
+int fgmres_core(lat_ctx* h, const GmresLevel& L, const double* b, double* x, bool x_zero, double rtol,
+                int max_it, int restart, bool op32, Prec&& precond, double* rel_out) {
   const int64_t n = h->n_krylov;
-  const int m = std::max(2, o->krylov_restart);
-  h->V.ensure((size_t)(m + 1) * n);
-  h->Zk.ensure((size_t)m * n);
-  h->Hh.ensure((size_t)(m + 1) * m + 4 * (m + 1));
-  h->gmres_small.ensure(3 * m + 8);
+  const int m = std::max(2, restart);
+  LAT_REQUIRE(m <= 190, LAT_EINVAL, "krylov_restart too large (max 190)");
+  L.V->ensure((size_t)(m + 1) * n);
+  L.Z->ensure((size_t)m * n);
+  L.H->ensure((size_t)(m + 1) * m + 4 * (m + 1));
+  L.small->ensure(3 * m + 8);
+  L.scal->ensure(8 + 4 * (m + 2));
   const int nb = red_blocks(n);
   h->dots_part.ensure((size_t)(m + 1) * nb);
-  double* sc = h->red_part.p + 3100;  // [0] nrm2, [1] est, [2..] h column, y
-  double* hcol = h->red_part.p + 3200;
-  double* h2 = h->red_part.p + 3400;
-  double* yv = h->red_part.p + 3600;
-  LAT_REQUIRE(m <= 190, LAT_EINVAL, "krylov_restart too large (max 190)");
-  double* w = h->kv_tmp[0].p;
+  double* sc = L.scal->p;              // [0] nrm2, [1] estimate
+  double* hcol = sc + 8;
+  double* h2 = hcol + (m + 2);
+  double* yv = h2 + (m + 2);
+  double* w = L.w;
   const int eb = ew_blocks(h, n);
   double* hp = h->h_pinned;
-  // ||b||
   dev_dot(h, n, b, b, sc);
   LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   LAT_CUDA(cudaStreamSynchronize(h->stream));
   const double bnorm = std::sqrt(hp[0]);
+  if (x_zero) LAT_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), h->stream));
   if (bnorm == 0.0) {
     LAT_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), h->stream));
     if (rel_out) *rel_out = 0;
@@ -1455,51 +1554,95 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
   }
   int total = 0;
   double rel = 1.0;
-  while (total < o->krylov_max_it) {
-    // r = b - A x
-    feti_operator(h, x, w, true);
-    LAT_LAUNCH(h, k_axpby<<<eb, 256, 0, h->stream>>>(n, 1.0, b, -1.0, w));
-    dev_dot(h, n, w, w, sc);
-    LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    LAT_CUDA(cudaStreamSynchronize(h->stream));
-    rel = std::sqrt(hp[0]) / bnorm;
-    if (rel <= o->krylov_rtol) break;
-    LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p));
-    LAT_LAUNCH(h, k_gmres_init<<<1, 1, 0, h->stream>>>(m, h->gmres_small.p, sc));
+  bool first = true;
+  while (total < max_it) {
+    // r = b - A x  (r = b for a zero start)
+    if (first && x_zero) {
+      LAT_CUDA(cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      rel = 1.0;
+    } else {
+      feti_operator(h, x, w, true, op32);
+      LAT_LAUNCH(h, k_axpby<<<eb, 256, 0, h->stream>>>(n, 1.0, b, -1.0, w));
+      dev_dot(h, n, w, w, sc);
+      LAT_CUDA(cudaMemcpyAsync(hp, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LAT_CUDA(cudaStreamSynchronize(h->stream));
+      rel = std::sqrt(hp[0]) / bnorm;
+      if (rel <= rtol) break;
+    }
+    first = false;
+    LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, L.V->p));
+    LAT_LAUNCH(h, k_gmres_init<<<1, 1, 0, h->stream>>>(m, L.small->p, sc));
     int j = 0;
-    for (; j < m && total < o->krylov_max_it; ++j, ++total) {
-      double* vj = h->V.p + (size_t)j * n;
-      double* zj = h->Zk.p + (size_t)j * n;
-      run_block_precond(h, vj, zj, o->pcg_iters, o->pcg_rtol);
-      feti_operator(h, zj, w, true);
+    for (; j < m && total < max_it; ++j, ++total) {
+      double* vj = L.V->p + (size_t)j * n;
+      double* zj = L.Z->p + (size_t)j * n;
+      precond(vj, zj);
+      feti_operator(h, zj, w, true, op32);
       // CGS with one re-orthogonalisation
       KernelTimer kt(h, "krylov_orth");
       for (int pass = 0; pass < 2; ++pass) {
-        LAT_LAUNCH(h, k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, h->V.p, w, h->dots_part.p));
+        LAT_LAUNCH(h, k_multidot_part<<<nb, 256, 0, h->stream>>>(n, j + 1, L.V->p, w, h->dots_part.p));
         LAT_LAUNCH(h, k_multidot_final<<<j + 1, 256, 0, h->stream>>>(nb, h->dots_part.p, pass == 0 ? hcol : h2));
-        LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j + 1, h->V.p, pass == 0 ? hcol : h2, -1.0, w));
+        LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j + 1, L.V->p, pass == 0 ? hcol : h2, -1.0, w));
       }
       LAT_LAUNCH(h, k_axpby<<<1, 256, 0, h->stream>>>(j + 1, 1.0, h2, 1.0, hcol));
       dev_dot(h, n, w, w, sc);
-      LAT_LAUNCH(h, k_givens<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, hcol, sc, sc + 1));
-      LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, h->V.p + (size_t)(j + 1) * n));
+      LAT_LAUNCH(h, k_givens<<<1, 1, 0, h->stream>>>(j, m, L.H->p, L.small->p, hcol, sc, sc + 1));
+      LAT_LAUNCH(h, k_scale_dev<<<eb, 256, 0, h->stream>>>(n, w, sc, L.V->p + (size_t)(j + 1) * n));
       LAT_CHECK_LAUNCH();
       LAT_CUDA(cudaMemcpyAsync(hp, sc, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LAT_CUDA(cudaStreamSynchronize(h->stream));
       rel = hp[1] / bnorm;
-      if (rel <= o->krylov_rtol || !(hp[0] > 0.0)) {
+      if (rel <= rtol || !(hp[0] > 0.0)) {
         ++j;
         ++total;
         break;
       }
     }
     // x += Z y
-    LAT_LAUNCH(h, k_gmres_solve<<<1, 1, 0, h->stream>>>(j, m, h->Hh.p, h->gmres_small.p, yv));
-    LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j, h->Zk.p, yv, 1.0, x));
+    LAT_LAUNCH(h, k_gmres_solve<<<1, 1, 0, h->stream>>>(j, m, L.H->p, L.small->p, yv));
+    LAT_LAUNCH(h, k_multi_axpy<<<eb, 256, 0, h->stream>>>(n, j, L.Z->p, yv, 1.0, x));
     LAT_CHECK_LAUNCH();
-    if (rel <= o->krylov_rtol) break;
+    if (rel <= rtol) break;
   }
   if (rel_out) *rel_out = rel;
+  return total;
+}
+
+}  // namespace
+
+// FGMRES on the saddle-point system (Section 3.3.1) with the FP64 reduced tangent action.  Its
+// preconditioner is the block preconditioner of Eq. (ifetidp_precond), or, in the mixed modes
+// with inner_its > 0, an inner flexible GMRES whose operator is the FP32 reduced tangent action
+// and whose preconditioner is the block preconditioner (mixed precision inside a flexible
+// Krylov method: the FP32 action and preconditioner only shape the search directions).
+int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o, double* rel_out) {
+  GmresLevel outer{&h->V, &h->Zk, &h->Hh, &h->gmres_small, &h->kscal[0], h->kv_tmp[0].p};
+  auto block = [&](const double* v, double* z) { run_block_precond(h, v, z, o->pcg_iters, o->pcg_rtol); };
+  int total;
+  if (h->prec != LAT_FP64 && o->inner_its > 0) {
+    GmresLevel inner{&h->V2, &h->Z2, &h->Hh2, &h->gmres_small2, &h->kscal[1], h->kv_tmp[1].p};
+    // an inner solve that misses inner_rtol within inner_its iterations (strongly indefinite
+    // states, e.g. the affine predictor of the first load step) spent its iterations for little
+    // gain: the rest of this solve then takes the block preconditioner directly (FGMRES allows
+    // the preconditioner to change from one iteration to the next)
+    bool stalled = false;
+    auto nested = [&](const double* v, double* z) {
+      if (stalled) {
+        block(v, z);
+        return;
+      }
+      double r = 0;
+      h->inner_its_total += fgmres_core(h, inner, v, z, true, o->inner_rtol, o->inner_its, o->inner_its, true,
+                                        block, &r);
+      stalled = r > o->inner_rtol;
+    };
+    total = fgmres_core(h, outer, b, x, false, o->krylov_rtol, o->krylov_max_it, o->krylov_restart, false, nested,
+                        rel_out);
+  } else {
+    total = fgmres_core(h, outer, b, x, false, o->krylov_rtol, o->krylov_max_it, o->krylov_restart, false, block,
+                        rel_out);
+  }
   if (h->prec == LAT_MIXED_BF16) {
     int fl = 0;
     LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -1538,14 +1681,20 @@ void run_axpy(lat_ctx* h, int64_t n, double a, const double* x, double* y) {
 // later iterations.  (With definite remaining blocks the coarse matrix loses definiteness when a
 // cell's local Schur complement does: inertia(K^s) = inertia(K_RR^s) + inertia(S^s); the edge
 // nodes tie the cells' free sides to their neighbours, which removes those modes.)
-void prepare_enriched(lat_ctx* h, const lat_newton_opts* o) {
-  run_prepare_solver(h, o);
+void prepare_enriched(lat_ctx* h, const lat_newton_opts* o, const double* u_glob) {
+  if (h->enrich_level < o->min_enrich) {
+    build_feti(h, std::min(o->min_enrich, o->max_enrich));
+    if (h->verbose)
+      std::fprintf(stderr, "[lattice] primal enrichment level %d (start): %d primal DOFs per cell, %lld coarse DOFs\n",
+                   h->enrich_level, h->n_P, (long long)h->n_primal);
+  }
+  run_prepare_solver(h, o, u_glob);
   while ((h->indefinite || h->coarse_indefinite) && h->enrich_level < o->max_enrich) {
     build_feti(h, h->enrich_level + 1);
     if (h->verbose)
       std::fprintf(stderr, "[lattice] primal enrichment level %d: %d primal DOFs per cell, %lld coarse DOFs\n",
                    h->enrich_level, h->n_P, (long long)h->n_primal);
-    run_prepare_solver(h, o);
+    run_prepare_solver(h, o, u_glob);
   }
 }
 
@@ -1565,6 +1714,10 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
   LAT_REQUIRE(o->max_enrich >= 0 && o->max_enrich <= 6, LAT_EINVAL, "max_enrich in [0, 6]");
   LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 1, LAT_EINVAL, "coarse_block_lu in {-1, 0, 1}");
+  LAT_REQUIRE(o->precond_tangent >= -1 && o->precond_tangent <= 1, LAT_EINVAL, "precond_tangent in {-1, 0, 1}");
+  LAT_REQUIRE(o->min_enrich >= 0 && o->min_enrich <= o->max_enrich, LAT_EINVAL, "min_enrich in [0, max_enrich]");
+  LAT_REQUIRE(o->inner_its >= 0 && o->inner_its <= 190, LAT_EINVAL, "inner_its in [0, 190]");
+  LAT_REQUIRE(o->inner_rtol >= 0 && o->inner_rtol < 1, LAT_EINVAL, "inner_rtol in [0, 1)");
 }
 
 // FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
@@ -1595,6 +1748,10 @@ extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
   o->interface_precond = 0;
   o->max_enrich = 3;
   o->coarse_block_lu = -1;
+  o->precond_tangent = -1;
+  o->min_enrich = 0;
+  o->inner_its = h->prec == LAT_FP64 ? 0 : 20;
+  o->inner_rtol = 1e-2;
   return LAT_OK;
 }
 
@@ -1613,6 +1770,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     double t0 = now_ms();
     bool neg = false;
     h->pcg_its_total = 0;
+    h->inner_its_total = 0;
     run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
     LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 at the initial guess");
     double rn = run_norm_free(h, h->r_glob.p);
@@ -1627,7 +1785,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
       double tb = now_ms();
       R.t_select_ms += tb - ta;
-      prepare_enriched(h, o);
+      prepare_enriched(h, o, u);
       double tc = now_ms();
       R.t_setup_ms += tc - tb;
       R.n_r_last = h->n_r;
@@ -1660,9 +1818,9 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       R.t_linesearch_ms += now_ms() - td;
       R.armijo_m_max = std::max(R.armijo_m_max, mm);
       if (h->verbose)
-        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d enrich=%d indef=%d/%d krylov=%d pcg=%lld (rel %.1e) m=%d%s\n",
+        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d enrich=%d indef=%d/%d krylov=%d inner=%lld pcg=%lld (rel %.1e) m=%d%s\n",
                      it, rn, rn / r0, h->n_r, h->n_keys, h->enrich_level, (int)h->indefinite, (int)h->coarse_indefinite,
-                     R.krylov_its_total, (long long)h->pcg_its_total, rel, mm,
+                     R.krylov_its_total, (long long)h->inner_its_total, (long long)h->pcg_its_total, rel, mm,
                      accepted ? "" : " REJECTED");
       if (!accepted) {
         // leave u and the residual buffers consistent with u
@@ -1682,6 +1840,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     R.iterations = it;
     R.r_norm = rn;
     R.pcg_its_total = (int32_t)h->pcg_its_total;
+    R.inner_its_total = (int32_t)h->inner_its_total;
     R.enrich_level = h->enrich_level;
     R.converged = (rn <= o->newton_rtol * r0 || rn <= floor) ? 1 : 0;
     du.release();
@@ -1695,8 +1854,7 @@ extern "C" lat_status lattice_prepare_solver(lat_handle h, const double* u, cons
   if (!h || !u) return LAT_EINVAL;
   return guard(h, [&] {
     check_opts(o);
-    (void)u;
-    prepare_enriched(h, o);
+    prepare_enriched(h, o, u);
   });
 }
 
@@ -1767,7 +1925,7 @@ extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_
     LAT_CUDA(cudaMemsetAsync(lam.p, 0, nd * sizeof(double), h->stream));
     LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
-    prepare_enriched(h, o);
+    prepare_enriched(h, o, u);
     R.n_r_last = h->n_r;
     double dn = bnorm;
     R.r0_norm = bnorm;

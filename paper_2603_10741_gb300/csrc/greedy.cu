@@ -389,6 +389,8 @@ extern "C" lat_status greedy_select_static(const double* T, int64_t n_rows, int3
                                            int32_t max_nr, int32_t* S, int32_t* n_r, double* alpha,
                                            void* cuda_stream) {
   if (!T || !S || !n_r || n_rows <= 0 || n_cols <= 0 || max_nr < 1) return LAT_EINVAL;
+  // each factor alone must fit before the products below are formed (no size_t wrap-around)
+  if ((uint64_t)n_rows > kStaticGreedyDoubles || (uint64_t)n_cols > kStaticGreedyDoubles) return LAT_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const int limit = (int)std::min<int64_t>({(int64_t)max_nr, (int64_t)n_cols, n_rows});
   if (static_layout(nullptr, n_rows, n_cols, limit).doubles > kStaticGreedyDoubles) return LAT_EINVAL;

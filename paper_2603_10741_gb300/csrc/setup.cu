@@ -603,7 +603,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
   rel(h->key_of_cell); rel(h->key_slot); rel(h->perm); rel(h->seg_ptr); rel(h->tile_seg);
   rel(h->tile_c0); rel(h->key_list); rel(h->solver_int); rel(h->delta_cell); rel(h->c_cell);
-  rel(h->G); rel(h->G16[0]); rel(h->G16[1]); rel(h->G16[2]); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->KRP); rel(h->Coarse);
+  rel(h->G); rel(h->G16[0]); rel(h->G16[1]); rel(h->G16[2]); rel(h->G16[3]); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->KRP); rel(h->Coarse);
   rel(h->CoarseInv); rel(h->CoarseInv32); rel(h->pcg_ws); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);
@@ -739,7 +739,9 @@ extern "C" lat_status lattice_set_timing(lat_handle h, int32_t enable) {
         h->ev_pool.push_back(pr.second);
       }
     h->ev.clear();
+    LAT_REQUIRE(enable >= 0 && enable <= 2, LAT_EINVAL, "enable is 0, 1 or 2");
     h->timing = enable != 0;
+    h->timing_apply_only = enable == 2;
   });
 }
 

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(128)
                const __nv_bfloat16* __restrict__ XT, const int* __restrict__ tile_seg,
                const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr, const int* __restrict__ perm,
                const double* __restrict__ cscale, const int* __restrict__ rr, const int* __restrict__ pdofs,
-               double* __restrict__ Y, int* __restrict__ err) {
+               double* __restrict__ Y, int* __restrict__ err, int mul_scale) {
   using C = TcCfg<TN, MW>;
   constexpr int STAGES = C::STAGES;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(128)
             if (pos >= c_end) continue;
             const int s = perm[pos];
             const double v = (double)__uint_as_float(r[j]);
-            Y[orow * n_cells + s] = gi < n_Kr ? v / cscale[s] : v;
+            Y[orow * n_cells + s] = gi < n_Kr ? (mul_scale ? v * cscale[s] : v / cscale[s]) : v;
           }
         }
       }
@@ -334,6 +334,17 @@ void run_g_to_bf16(lat_ctx* h, size_t n) {
                                                                       h->G.p + (size_t)lo_r * nR + lo_c, cnt,
                                                                       h->G16[mode].p));
   }
+  // the dual Schur complements S_DD [keys][n_D][n_D] of the Dirichlet interface preconditioner
+  const int nD = nR - nI;
+  if (nD > 0 && h->SDD.p) {
+    const int MT = div_up(nD, TM), KP = std::max(1, div_up(nD, TK));
+    const int64_t cnt = keys * MT * KP * A_ELEMS;
+    h->G16[3].ensure((size_t)2 * cnt);
+    h->g16_ld[3] = KP;
+    h->g16_lo[3] = cnt;
+    LAT_LAUNCH(h, k_g_tile<<<div_up(cnt, 256), 256, 0, h->stream>>>(keys, nD, nD, MT, KP, nD, (int64_t)nD * nD,
+                                                                      h->SDD.p, cnt, h->G16[3].p));
+  }
   LAT_CHECK_LAUNCH();
 }
 
@@ -359,7 +370,31 @@ void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int*
   KernelTimer kt(h, tg[mode]);
   LAT_LAUNCH(h, (k_local_tc<TN, MW><<<grid, 128, C::SMEM_BYTES, h->stream>>>(
                     h->n_cells, nKr, h->n_P, MT, KP, h->g16_lo[mode], h->G16[mode].p, h->Xb16.p, tseg, tc0,
-                    h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p)));
+                    h->seg_ptr.p, h->perm.p, h->c_cell.p, rr, h->pdofs.p, Y, h->flag.p, 0)));
+  LAT_CHECK_LAUNCH();
+}
+
+// the Dirichlet interface preconditioner's local products y_D = c_s S_DD x_D on the same tiles
+// (dual rows and columns, no corner rows, scaled by c_s)
+template <int TN>
+void launch_sdd_tc(lat_ctx* h, const double* X, double* Y) {
+  using C = TcCfg<TN, 1>;
+  const int nD = h->n_R - h->n_I;
+  const int MT = div_up(nD, TM);
+  const int KP = h->g16_ld[3];
+  const int* rd = h->rdofs.p + h->n_I;
+  const int KPmax = std::max(1, div_up(h->n_R, TK));
+  h->Xb16.ensure((size_t)h->max_tiles * 2 * KPmax * C::B_ELEMS);
+  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(h->max_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nD, KP, X, h->tile_seg.p,
+                                                                              h->tile_c0.p, h->seg_ptr.p, h->perm.p,
+                                                                              rd, h->Xb16.p));
+  LAT_CUDA(cudaFuncSetAttribute(k_local_tc<TN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)C::SMEM_BYTES));
+  dim3 grid(h->max_tiles, MT);
+  KernelTimer kt(h, "dual_schur_tc");
+  LAT_LAUNCH(h, (k_local_tc<TN, 1><<<grid, 128, C::SMEM_BYTES, h->stream>>>(
+                    h->n_cells, nD, 0, MT, KP, h->g16_lo[3], h->G16[3].p, h->Xb16.p, h->tile_seg.p, h->tile_c0.p,
+                    h->seg_ptr.p, h->perm.p, h->c_cell.p, rd, h->pdofs.p, Y, h->flag.p, 1)));
   LAT_CHECK_LAUNCH();
 }
 
@@ -372,3 +407,5 @@ void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int*
 void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
   launch_tc<64, 1>(h, X, Y, mode, h->tile_seg.p, h->tile_c0.p, h->max_tiles);
 }
+
+void run_sdd_tc(lat_ctx* h, const double* X, double* Y) { launch_sdd_tc<64>(h, X, Y); }

@@ -56,7 +56,8 @@ class NewtonOpts(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_max_it", C.c_int32), ("krylov_rtol", C.c_double),
                 ("krylov_max_it", C.c_int32), ("krylov_restart", C.c_int32), ("pcg_iters", C.c_int32),
                 ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32),
-                ("max_enrich", C.c_int32), ("coarse_block_lu", C.c_int32)]
+                ("max_enrich", C.c_int32), ("coarse_block_lu", C.c_int32), ("precond_tangent", C.c_int32),
+                ("min_enrich", C.c_int32), ("inner_its", C.c_int32), ("inner_rtol", C.c_double)]
 
 
 class NewtonReport(C.Structure):
@@ -64,7 +65,7 @@ class NewtonReport(C.Structure):
                 ("r_norm", C.c_double), ("n_r_last", C.c_int32), ("krylov_its_total", C.c_int32),
                 ("armijo_m_max", C.c_int32), ("t_residual_ms", C.c_double), ("t_select_ms", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_linesearch_ms", C.c_double),
-                ("pcg_its_total", C.c_int32), ("enrich_level", C.c_int32)]
+                ("pcg_its_total", C.c_int32), ("enrich_level", C.c_int32), ("inner_its_total", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -163,13 +164,16 @@ def greedy_select_static(T, eps, max_nr, stream=None):
     tensor [n_cols, n_rows] (column s contiguous); S and alpha are allocated here by torch, the
     caller's allocator, and passed in.  Returns (S [n_r] int32, alpha [n_r, n_cols]).
     """
+    if T.dtype != torch.float64 or not T.is_cuda or T.dim() != 2 or not T.is_contiguous():
+        raise ValueError("T must be a contiguous 2-D float64 CUDA tensor [n_cols, n_rows]")
     n_cols, n_rows = T.shape
-    stream = torch.cuda.current_stream() if stream is None else stream
-    S = torch.zeros(max_nr, dtype=torch.int32, device=T.device)
-    alpha = torch.zeros((max_nr, n_cols), dtype=torch.float64, device=T.device)
-    n_r = C.c_int32(0)
-    st = lib().greedy_select_static(_ptr(T), n_rows, n_cols, float(eps), int(max_nr), _ptr(S), C.byref(n_r),
-                                    _ptr(alpha), C.c_void_p(stream.cuda_stream))
+    with torch.cuda.device(T.device):
+        stream = torch.cuda.current_stream() if stream is None else stream
+        S = torch.zeros(max_nr, dtype=torch.int32, device=T.device)
+        alpha = torch.zeros((max_nr, n_cols), dtype=torch.float64, device=T.device)
+        n_r = C.c_int32(0)
+        st = lib().greedy_select_static(_ptr(T), n_rows, n_cols, float(eps), int(max_nr), _ptr(S), C.byref(n_r),
+                                        _ptr(alpha), C.c_void_p(stream.cuda_stream))
     if st != 0:
         raise LatticeError(st, "greedy_select_static failed (sizes beyond the 16 MiB workspace give LAT_EINVAL)")
     k = n_r.value

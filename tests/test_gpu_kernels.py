@@ -181,6 +181,19 @@ def test_force_all_apply_is_per_cell(L):
     lat.close()
 
 
+def _greedy_matches_oracle(prob, ul, eps, S, al):
+    """Algorithm 1 run by the oracle on its own snapshot matrix of every cell (reduced rule at the
+    same state): the same principal set in the same order, the same coefficients, and at the end
+    of the oracle's trace the certified bound max_s ||Delta^s||_inf <= eps, unless the trace
+    stopped at the cap of 256 principals."""
+    T = OC.snapshots(prob.cell, ul, prob.mu_cells, prob.lam)
+    g = OG.greedy(T, eps, 256)
+    assert S.tolist() == g.S.tolist()
+    al_ref = OG.alpha_triangular(T, g)
+    assert np.abs(al - al_ref).max() <= 1e-9 * max(1.0, np.abs(al_ref).max())
+    assert g.max_res[-1] <= eps or len(g.S) == 256
+
+
 def test_full_size_ring32_sampled(L):
     """The 32x32 ring lattice (0.56 M DOF) at full size: residual, tangents and snapshots of 64
     seeded cells, the greedy on the full snapshot matrix and the apply on sampled cells."""
@@ -204,6 +217,7 @@ def test_full_size_ring32_sampled(L):
     al = sel["alpha"].cpu().numpy()
     S = sel["S"].cpu().numpy()
     assert np.abs(al[:, S] - np.eye(len(S))).max() < 1e-9
+    _greedy_matches_oracle(prob, ul, 3e-4, S, al)
     Kp = sel["Kp"].cpu().numpy()
     assert _rel(Kp[:4], OC.tangent(prob.cell, ul[S[:4]], prob.mu_cells[S[:4]], prob.lam)) < RTOL64
     X = latgen.uniform_field((lat.sizes.n_loc, lat.sizes.n_cells), 7)
@@ -237,6 +251,7 @@ def test_full_size_strut10_sampled(L):
     al = sel["alpha"].cpu().numpy()
     S = sel["S"].cpu().numpy()
     assert np.abs(al[:, S] - np.eye(len(S))).max() < 1e-9
+    _greedy_matches_oracle(prob, ul, 5e-3, S, al)
     Kp = sel["Kp"].cpu().numpy()
     assert _rel(Kp[:2], OC.tangent(prob.cell, ul[S[:2]], prob.mu_cells[S[:2]], prob.lam)) < RTOL64
     X = latgen.uniform_field((lat.sizes.n_loc, lat.sizes.n_cells), 19)

@@ -67,7 +67,9 @@ def test_force_all_local_inverse_is_exact(L, name):
     lat = L.Lattice.from_case(case)
     ud = torch.tensor(_u0(prob, 1, 0.002, 1), device="cuda")
     lat.select_principal_cells(ud, 0.0, 1, force_all=True)
-    lat.lattice_prepare_solver(ud)
+    # the local blocks from the full tangent (the material-part option builds them from another
+    # matrix, so it gives a preconditioner, not the inverse of K~)
+    lat.lattice_prepare_solver(ud, lat.lattice_default_opts(precond_tangent=0))
     s = lat.sizes
     rng = np.random.default_rng(3)
     v = lat.feti_from_global(torch.tensor(rng.uniform(-1, 1, s.n_dof), device="cuda"))
@@ -83,19 +85,22 @@ def test_force_all_local_inverse_is_exact(L, name):
 
 
 @pytest.mark.parametrize("force_all", [True, False])
-@pytest.mark.parametrize("name", ["ring4", "strut2"])
-def test_krylov_solve_matches_direct_solve(L, name, force_all):
+@pytest.mark.parametrize("name,strain,pre", [("ring4", 0.01, -1), ("strut2", 0.002, 0), ("strut2", 0.002, 1),
+                                             ("strut2", 0.01, 1)])
+def test_krylov_solve_matches_direct_solve(L, name, strain, pre, force_all):
     """The FGMRES solution on the FETI-DP saddle point equals the oracle's direct solve of the
-    assembled (exact, or reduced sum_r alpha_r^s K^r) tangent system for the Newton rhs -r."""
+    assembled (exact, or reduced sum_r alpha_r^s K^r) tangent system for the Newton rhs -r.
+    On the strut cells at 0.2 % compression the corner-only local blocks of the full tangent are
+    still definite; at 1 % they are not, and the preconditioner is built from the material part
+    of the principal tangents (pre = 1), which does not change the solution."""
     case = latgen.make_case(name)
-    # a state below the first local instability: with corner-only primal DOFs the thin strut
-    # cells' remaining-DOF matrices lose definiteness near 1 % compression (Section 3.3.2)
-    case.total_strain = 0.01 if name == "ring4" else 0.002
+    case.total_strain = strain
     prob = Problem(case)
     u0 = _u0(prob, 1, 0.0005 if name == "ring4" else 0.0001, 2)
     lat = L.Lattice.from_case(case)
     eps = 1e-3
-    opts = lat.lattice_default_opts(eps=eps, force_all=int(force_all), krylov_rtol=1e-12, krylov_max_it=3000)
+    opts = lat.lattice_default_opts(eps=eps, force_all=int(force_all), krylov_rtol=1e-12, krylov_max_it=3000,
+                                    precond_tangent=pre)
     ud = torch.tensor(u0, device="cuda")
     sel = lat.select_principal_cells(ud, eps, 256, force_all=force_all)
     lat.lattice_prepare_solver(ud, opts)
@@ -368,3 +373,71 @@ def test_bf16_tensor_core_3d_blocks(L):
     ref, got = outs
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < 1e-4, err
+
+
+def _oracle_kinv_rom(prob, ul, eps, v_glob):
+    """The oracle's reading of K^-rom (Section 3.3.1 with the principal-cell ROM of the local DD
+    operators): the oracle's greedy on its own snapshots picks the principals; every cell s is
+    tied to the principal r(s) whose snapshot is nearest in direction (largest cosine) with the
+    scale c_s = |t^s| cos / |t^r(s)|; K^-rom is then the exact inverse of the partially assembled
+    matrix built from the per-cell matrices c_s K^r(s) (corners primal), applied by a direct
+    sparse solve to the saddle-point image of the global vector v_glob.  Returns the solution on
+    the remaining (R) unknowns as {(cell, local dof): value}, and the FETI index sets."""
+    import scipy.sparse as sp
+    from oracle.fetidp import FetiDP
+    T = OC.snapshots(prob.cell, ul, prob.mu_cells, prob.lam)
+    g = OG.greedy(T, eps, 256)
+    nrm = np.linalg.norm(T, axis=0)
+    cosv = (T[:, g.S].T @ T) / (nrm[g.S][:, None] * nrm[None, :])       # [N_r, N_s]
+    r_of = np.argmax(cosv, axis=0)
+    c = nrm * cosv[r_of, np.arange(T.shape[1])] / nrm[g.S][r_of]
+    Kp = OC.tangent(prob.cell, ul[g.S], prob.mu_cells[g.S], prob.lam)
+    Khat = c[:, None] * Kp[r_of]
+    fe = FetiDP(prob)
+    idx = fe._index()
+    n = fe.n_r + fe.n_p
+    cell = prob.cell
+    ri, ci = idx[:, cell.rows], idx[:, cell.cols]
+    keep = (ri >= 0) & (ci >= 0)
+    Kt = sp.csr_matrix((Khat[keep], (ri[keep], ci[keep])), shape=(n, n)).tocsc()
+    rhs = np.zeros(n)
+    cd = prob.cell_dofs
+    ok = idx >= 0
+    rhs[idx[ok]] = v_glob[cd[ok]]          # every copy (remaining) and each primal DOF once
+    x = sp.linalg.spsolve(Kt, rhs)
+    return x, idx, fe, len(g.S)
+
+
+def test_bf16_tensor_core_kinv_matches_oracle_elementwise(L):
+    """BF16 mode on the 8x8 ring lattice with few principals (eps 1e-2: the key segments are long
+    enough for the tcgen05 product): K^-rom applied to the saddle-point image of a seeded global
+    vector, element by element on every remaining local DOF, against the oracle's direct solve of
+    the same ROM-partially-assembled matrix (FP64).  The local inverse products run on the tensor
+    cores with BF16 operand pairs and FP32 accumulation, the coarse solve in FP64."""
+    case = latgen.make_case("ring8")
+    prob = Problem(case)
+    u0 = _u0(prob, 1, 0.0005, 4)
+    ul = prob.local(u0)
+    rng = np.random.default_rng(21)
+    vg = rng.uniform(-1, 1, prob.n_dof)
+    vg[prob.fixed] = 0.0
+    x_ref, idx, fe, n_r = _oracle_kinv_rom(prob, ul, 1e-2, vg)
+    lat = L.Lattice.from_case(case, 2)
+    ud = torch.tensor(u0, device="cuda")
+    sel = lat.select_principal_cells(ud, 1e-2, 256)
+    assert sel["n_r"] == n_r
+    lat.lattice_set_timing(True)
+    lat.lattice_prepare_solver(ud, lat.lattice_default_opts(eps=1e-2, precond_tangent=0, max_enrich=0))
+    s = lat.sizes
+    v = lat.feti_from_global(torch.tensor(vg, device="cuda"))
+    w = lat.feti_apply(1, v).cpu().numpy()
+    _, n_tc = lat.lattice_kernel_time("local_tc")
+    lat.lattice_set_timing(False)
+    assert n_tc > 0, "the tensor-core product did not run"
+    wl = w[: s.n_loc * s.n_cells].reshape(s.n_loc, s.n_cells)
+    rmask = fe.r_index >= 0                      # [N_s, n_loc] remaining, non-fixed entries
+    got = wl.T[rmask]
+    ref = x_ref[idx[rmask]]
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    assert err < 2e-4, err
+    lat.close()

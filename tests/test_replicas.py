@@ -52,9 +52,10 @@ def _reference_rank(rank, world, port, out):
     sys.path.insert(0, ROOT)
     import bench
     called = []
-    bench.oracle_step_fn = lambda case, step: (lambda: called.append(1), 1000)   # stand-in step
+    bench.oracle_apply_fn = lambda case, step, n: (lambda: called.append(1), 1000, "stand-in")   # stand-in step
     import argparse
-    args = argparse.Namespace(impl="reference", gpus=world, steps=2, warmup=3, case="ring32", state_step=10)
+    args = argparse.Namespace(impl="reference", gpus=world, steps=2, warmup=3, case="strut20", state_step=1,
+                              sample_cells=8)
     rc = bench.run_reference(args)
     out[rank] = (rc, len(called))
 
