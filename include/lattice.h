@@ -212,10 +212,13 @@ typedef struct {
                               the points j/2^L of each edge) for all cells, and kept */
   int32_t coarse_block_lu; /* coarse solves of a block-tridiagonal coarse matrix: 1 block LU in
                               FP64 (two sequential sweeps over the cell layers, factors N m^3,
-                              no explicit inverse), 0 the explicit inverse (N^2 m^3 to build,
-                              one dense product per solve; FP32 copy in the mixed modes), -1
-                              (default) block LU when the explicit inverse would hold more than
-                              8192^2 entries (N blocks of size m, N m > 8192) */
+                              no explicit inverse; a sweep step is one thread-block cluster for
+                              blocks up to 512 rows, one launch over the whole GPU for larger
+                              ones), 2 block LU with the whole-GPU steps at any block size, 0 the
+                              explicit inverse (N^2 m^3 to build, one dense product per solve;
+                              FP32 copy in the mixed modes), -1 (default) block LU when the
+                              explicit inverse would hold more than 8192^2 entries (N blocks of
+                              size m, N m > 8192) */
   int32_t precond_tangent; /* principal tangents the preconditioner's local blocks are built from:
                               0 the full tangent K^r (Section 3.1.4), 1 its material part (the
                               geometric stress term delta_ij sigma_kl of D dropped: positive

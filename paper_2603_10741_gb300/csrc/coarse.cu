@@ -307,6 +307,60 @@ __global__ void __launch_bounds__(256) k_coarse_dinv(int N, int m, const double*
   if (lane == 0) w[t] = acc;
 }
 
+// Wide block steps for large blocks: one launch per step of the recurrence, a warp per row of
+// the m x m block over the whole GPU (a 16-CTA cluster cannot stream an m = 1323 block of 14 MB
+// fast enough: ~70 us per step measured on the 20^3 strut lattice, against a few us here).
+//   k_cb_rhs:     rhs in block layout from the primal vector (0 on padding)
+//   k_cb_step:    out = rs - M vin for one block (M row-major m x m)
+//   k_cb_scatter: block layout -> primal vector
+__global__ void k_cb_rhs(int64_t rows, const int* __restrict__ perm, const double* __restrict__ g,
+                         double* __restrict__ rhs) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows) return;
+  const int p = perm[t];
+  rhs[t] = p >= 0 ? g[p] : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_cb_step(int m, const double* __restrict__ M, const double* __restrict__ vin,
+                                                 const double* __restrict__ rs, double* __restrict__ out) {
+  // m is even (padded blocks): a row is m / 2 16-byte pairs, eight loads in flight per lane
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const double2* a = reinterpret_cast<const double2*>(M + (size_t)row * m);
+  const double2* v = reinterpret_cast<const double2*>(vin);
+  const int h2 = m >> 1;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int k = lane;
+  for (; k + 96 < h2; k += 128) {
+    const double2 p0 = __ldcs(a + k), p1 = __ldcs(a + k + 32), p2 = __ldcs(a + k + 64), p3 = __ldcs(a + k + 96);
+    const double2 x0 = __ldg(v + k), x1 = __ldg(v + k + 32), x2 = __ldg(v + k + 64), x3 = __ldg(v + k + 96);
+    acc[0] = fma(p0.x, x0.x, acc[0]);
+    acc[1] = fma(p0.y, x0.y, acc[1]);
+    acc[2] = fma(p1.x, x1.x, acc[2]);
+    acc[3] = fma(p1.y, x1.y, acc[3]);
+    acc[4] = fma(p2.x, x2.x, acc[4]);
+    acc[5] = fma(p2.y, x2.y, acc[5]);
+    acc[6] = fma(p3.x, x3.x, acc[6]);
+    acc[7] = fma(p3.y, x3.y, acc[7]);
+  }
+  for (; k < h2; k += 32) {
+    const double2 p = __ldcs(a + k), x = __ldg(v + k);
+    acc[0] = fma(p.x, x.x, acc[0]);
+    acc[1] = fma(p.y, x.y, acc[1]);
+  }
+  const double s = warp_sum(((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+  if (lane == 0) out[row] = rs[row] - s;
+}
+
+__global__ void k_cb_scatter(int64_t rows, const int* __restrict__ perm, const double* __restrict__ xb,
+                             double* __restrict__ x) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= rows) return;
+  const int p = perm[t];
+  if (p >= 0) x[p] = xb[t];
+}
+
 template <bool FWD>
 void launch_sweep(lat_ctx* h, const double* M, const double* rhs, double* out) {
   const int C = h->cb_cluster, R = div_up(h->cb_m, C);
@@ -473,8 +527,31 @@ bool coarse_block_plan(lat_ctx* h) {
 // x_P = S_PP^{-1} g_P by the block-LU sweeps (FP64)
 void run_coarse_block_solve(lat_ctx* h, const double* g, double* x) {
   const int N = h->cb_n, m = h->cb_m;
-  launch_sweep<true>(h, h->cb_Ut.p, g, h->cb_y.p);
   const int64_t rows = (int64_t)N * m;
+  const size_t mm = (size_t)m * m;
+  if (h->cb_wide) {
+    // y_b = g_b - U_{b-1}^T y_{b-1};  w = D^{-1} y;  x_b = w_b - U_b x_{b+1}
+    h->cb_r.ensure((size_t)rows);
+    double *rb = h->cb_r.p, *y = h->cb_y.p, *w = h->cb_w.p;
+    const int rb_grid = (int)div_up(rows, 256), st_grid = (int)div_up((int64_t)m * 32, 256);
+    LAT_LAUNCH(h, k_cb_rhs<<<rb_grid, 256, 0, h->stream>>>(rows, h->cb_perm.p, g, rb));
+    LAT_CUDA(cudaMemcpyAsync(y, rb, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    for (int b = 1; b < N; ++b)
+      LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, h->cb_Ut.p + (size_t)(b - 1) * mm,
+                                                              y + (size_t)(b - 1) * m, rb + (size_t)b * m,
+                                                              y + (size_t)b * m));
+    LAT_LAUNCH(h, k_coarse_dinv<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv.p, y, w));
+    double* xb = rb;   // the right-hand sides are consumed
+    LAT_CUDA(cudaMemcpyAsync(xb + (size_t)(N - 1) * m, w + (size_t)(N - 1) * m, m * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+    for (int b = N - 2; b >= 0; --b)
+      LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, h->cb_U.p + (size_t)b * mm, xb + (size_t)(b + 1) * m,
+                                                              w + (size_t)b * m, xb + (size_t)b * m));
+    LAT_LAUNCH(h, k_cb_scatter<<<rb_grid, 256, 0, h->stream>>>(rows, h->cb_perm.p, xb, x));
+    LAT_CHECK_LAUNCH();
+    return;
+  }
+  launch_sweep<true>(h, h->cb_Ut.p, g, h->cb_y.p);
   LAT_LAUNCH(h, k_coarse_dinv<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv.p, h->cb_y.p,
                                                                              h->cb_w.p));
   LAT_CHECK_LAUNCH();

@@ -133,13 +133,14 @@ struct lat_ctx {
   bool coarse_blocked = false;
   int cb_n = 0, cb_m = 0;                 // number of blocks, padded block size
   bool cb_solve = false;                  // FP64 coarse solves by block LU (no dense inverse)
+  bool cb_wide = false;                   // block-LU steps as full-GPU launches (else cluster sweeps)
   int cb_cluster = 0, cb_pre = 0;         // CTAs per cluster of the sweeps, rows prefetched
   size_t cb_shm = 0;
   DBuf<int64_t> cb_dest;                  // coarse entry -> index in [A blocks | B blocks], -1 skip
   DBuf<int> cb_perm;                      // block position (b*m + l) -> primal DOF or -1
   std::vector<int32_t> h_cell_layer;
   DBuf<double> cb_A, cb_B, cb_Dinv, cb_Einv, cb_U, cb_V, cb_T, cb_X;
-  DBuf<double> cb_Ut, cb_y, cb_w;       // block-LU solves: U_i^T, forward result, D^-1 y
+  DBuf<double> cb_Ut, cb_y, cb_w, cb_r; // block-LU solves: U_i^T, forward result, D^-1 y, rhs / x
 
   // selection state
   int n_r = 0;
@@ -414,6 +415,7 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
 bool coarse_block_plan(lat_ctx* h);
 constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
+constexpr int kWideSweepRows = 512;           // block-LU steps of larger blocks run over the whole GPU
 void run_coarse_block_solve(lat_ctx* h, const double* g, double* x);
 void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)

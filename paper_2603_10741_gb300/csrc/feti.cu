@@ -1127,9 +1127,10 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_gl
   // inverse is kept while it is small; its N^2 m^3 build and N^2 m^2 storage decide beyond that.
   const int64_t np = h->n_primal;
   const int want = o ? o->coarse_block_lu : -1;
+  h->cb_wide = want == 2 || h->cb_m > kWideSweepRows;
   h->cb_solve = np > 0 && h->coarse_blocked &&
-                (want == 1 || (want < 0 && (int64_t)h->cb_n * h->cb_m > kDenseCoarseLimit)) &&
-                coarse_block_plan(h);
+                (want >= 1 || (want < 0 && (int64_t)h->cb_n * h->cb_m > kDenseCoarseLimit)) &&
+                (h->cb_wide || coarse_block_plan(h));
   if (h->cb_solve) {
     h->CoarseInv.release();
     h->CoarseInv32.release();
@@ -1713,7 +1714,7 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->pcg_rtol >= 0 && o->pcg_rtol < 1, LAT_EINVAL, "pcg_rtol in [0, 1)");
   LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
   LAT_REQUIRE(o->max_enrich >= 0 && o->max_enrich <= 6, LAT_EINVAL, "max_enrich in [0, 6]");
-  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 1, LAT_EINVAL, "coarse_block_lu in {-1, 0, 1}");
+  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 2, LAT_EINVAL, "coarse_block_lu in {-1, 0, 1, 2}");
   LAT_REQUIRE(o->precond_tangent >= -1 && o->precond_tangent <= 1, LAT_EINVAL, "precond_tangent in {-1, 0, 1}");
   LAT_REQUIRE(o->min_enrich >= 0 && o->min_enrich <= o->max_enrich, LAT_EINVAL, "min_enrich in [0, max_enrich]");
   LAT_REQUIRE(o->inner_its >= 0 && o->inner_its <= 190, LAT_EINVAL, "inner_its in [0, 190]");

@@ -459,7 +459,8 @@ void build_feti_impl(lat_ctx* h, int level) {
     };
     Blocking hi = blocking(true), lo = blocking(false);
     const Blocking& B = lo.m < hi.m ? lo : hi;
-    const int N = B.N, m = B.m;
+    // blocks padded to an even size (identity on the padding): 16-byte rows for the sweeps
+    const int N = B.N, m = (B.m + 1) & ~1;
     bool tri = N >= 2;
     std::vector<int64_t> dest(crow.size(), -1);
     const size_t mm = (size_t)m * m;

@@ -234,8 +234,9 @@ def test_newton_bf16_mode_ring4(L):
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_blocked_coarse_inverse_matches_dense(L, precision):
-    """Coarse solves on the 8x8 ring lattice: the block-LU sweeps over the cell layers and the
-    block-tridiagonal explicit inverse equal the dense inverse of the unlayered coarse matrix, and
+    """Coarse solves on the 8x8 ring lattice: the block-LU sweeps over the cell layers (one
+    cluster per sweep, and one whole-GPU launch per step) and the block-tridiagonal explicit
+    inverse equal the dense inverse of the unlayered coarse matrix, and
     with every cell principal K^-rom stays the exact inverse of K~ in FP64.  In the FP32 mode
     (FP32 local inverses; the block-LU solve stays FP64, the explicit inverse is applied as an FP32
     copy) the three agree to FP32 rounding."""
@@ -245,7 +246,7 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
     arrays = L.case_arrays(case)
     outs = []
     tol = 1e-9 if precision == 0 else 1e-5
-    for layered, block_lu in ((True, 1), (True, 0), (False, 0)):
+    for layered, block_lu in ((True, 1), (True, 2), (True, 0), (False, 0)):
         a = dict(arrays)
         if not layered:
             a["cell_layer"] = None
@@ -253,7 +254,7 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
         lat.select_principal_cells(ud, 0.0, 1, force_all=True)
         lat.lattice_prepare_solver(ud, lat.lattice_default_opts(coarse_block_lu=block_lu))
         s = lat.sizes
-        assert s.coarse_block_lu == (1 if layered and block_lu else 0)
+        assert s.coarse_block_lu == (1 if layered and block_lu else 0)   # 2: block LU, full-GPU steps
         if layered:
             assert s.n_coarse_blocks >= 2 and s.coarse_block > 0
         rng = np.random.default_rng(7)
@@ -268,9 +269,10 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
             assert err < 1e-9, (layered, block_lu, err)
         outs.append(back[:nd].cpu().numpy())
         lat.close()
-    ref = np.abs(outs[2]).max()
-    assert np.abs(outs[0] - outs[2]).max() < tol * ref
-    assert np.abs(outs[1] - outs[2]).max() < (1e-10 if precision == 0 else tol) * ref
+    ref = np.abs(outs[3]).max()
+    assert np.abs(outs[0] - outs[3]).max() < tol * ref
+    assert np.abs(outs[1] - outs[3]).max() < tol * ref
+    assert np.abs(outs[2] - outs[3]).max() < (1e-10 if precision == 0 else tol) * ref
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
