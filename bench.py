@@ -270,8 +270,9 @@ def kernel_work(name, s, n_r, mixed):
         (X and Y streamed once, alpha and the principal values read once), b = 4 or 8;
     apply_percell: the plain path, b nnz N_s + 2 b n_loc N_s bytes;
     coarse_solve: block-LU solve of the block-tridiagonal coarse matrix (N blocks of size m),
-        2 (3 N - 2) m^2 FP64 flops; coarse_gemv: the explicit coarse inverse, 2 n_primal^2 FP64
-        flops (FP32 copy in the mixed modes: 4 n_primal^2 bytes).
+        2 (3 N - 2) m^2 FP64 flops (FP64 ALU bound), or in the mixed modes the FP32 factor copies
+        streamed once, 4 (3 N - 2) m^2 bytes (HBM bound); coarse_gemv: the explicit coarse
+        inverse, 2 n_primal^2 FP64 flops (FP32 copy in the mixed modes: 4 n_primal^2 bytes).
     """
     n_s, n_loc, nnz = s.n_cells, s.n_loc, s.nnz
     n_rr, n_p = s.n_r_local, s.n_p_local
@@ -296,6 +297,10 @@ def kernel_work(name, s, n_r, mixed):
         return b * nnz * n_s + 2 * b * n_loc * n_s, "hbm"
     if name == "coarse_solve" and s.n_coarse_blocks:
         nb, mb = s.n_coarse_blocks, s.coarse_block
+        if mixed:
+            # FP32 copies of the factors U_i, U_i^T (N - 1 blocks each) and D_i^-1 (N blocks), each
+            # streamed once per solve
+            return 4.0 * (3 * nb - 2) * mb * mb, "hbm"
         return 2.0 * (3 * nb - 2) * mb * mb, "fp64"
     if name == "coarse_gemv":
         if mixed:

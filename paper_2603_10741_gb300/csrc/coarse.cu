@@ -323,34 +323,91 @@ __global__ void k_cb_rhs(int64_t rows, const int* __restrict__ perm, const doubl
 
 __global__ void __launch_bounds__(256) k_cb_step(int m, const double* __restrict__ M, const double* __restrict__ vin,
                                                  const double* __restrict__ rs, double* __restrict__ out) {
-  // m is even (padded blocks): a row is m / 2 16-byte pairs, eight loads in flight per lane
+  // m is even (padded blocks): a row is m / 2 16-byte pairs; every lane issues all its loads of a
+  // chunk (up to 12 in flight) before the first multiply-add
+  constexpr int U = 12;
   const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   const double2* a = reinterpret_cast<const double2*>(M + (size_t)row * m);
   const double2* v = reinterpret_cast<const double2*>(vin);
   const int h2 = m >> 1;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int k = lane;
-  for (; k + 96 < h2; k += 128) {
-    const double2 p0 = __ldcs(a + k), p1 = __ldcs(a + k + 32), p2 = __ldcs(a + k + 64), p3 = __ldcs(a + k + 96);
-    const double2 x0 = __ldg(v + k), x1 = __ldg(v + k + 32), x2 = __ldg(v + k + 64), x3 = __ldg(v + k + 96);
-    acc[0] = fma(p0.x, x0.x, acc[0]);
-    acc[1] = fma(p0.y, x0.y, acc[1]);
-    acc[2] = fma(p1.x, x1.x, acc[2]);
-    acc[3] = fma(p1.y, x1.y, acc[3]);
-    acc[4] = fma(p2.x, x2.x, acc[4]);
-    acc[5] = fma(p2.y, x2.y, acc[5]);
-    acc[6] = fma(p3.x, x3.x, acc[6]);
-    acc[7] = fma(p3.y, x3.y, acc[7]);
+  double acc0 = 0.0, acc1 = 0.0;
+  for (int k0 = 0; k0 < h2; k0 += 32 * U) {
+    double2 p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + lane + 32 * u;
+      p[u] = k < h2 ? __ldcs(a + k) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + lane + 32 * u;
+      if (k < h2) {
+        const double2 x = __ldg(v + k);
+        acc0 = fma(p[u].x, x.x, acc0);
+        acc1 = fma(p[u].y, x.y, acc1);
+      }
+    }
   }
-  for (; k < h2; k += 32) {
-    const double2 p = __ldcs(a + k), x = __ldg(v + k);
-    acc[0] = fma(p.x, x.x, acc[0]);
-    acc[1] = fma(p.y, x.y, acc[1]);
-  }
-  const double s = warp_sum(((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7])));
+  const double s = warp_sum(acc0 + acc1);
   if (lane == 0) out[row] = rs[row] - s;
+}
+
+// the same with FP32 factors (mixed modes): products in FP32, vectors FP64; m a multiple of 4.
+// Every lane issues all its row loads before the first multiply-add (up to 12 16-byte loads in
+// flight per lane), so that a step's few hundred warps keep enough bytes in flight to stream the
+// block at HBM speed; longer rows loop.
+__global__ void __launch_bounds__(256) k_cb_step32(int m, const float* __restrict__ M, const double* __restrict__ vin,
+                                                   const double* __restrict__ rs, double* __restrict__ out) {
+  constexpr int U = 12;
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= m) return;
+  const float4* a = reinterpret_cast<const float4*>(M + (size_t)row * m);
+  const double2* v = reinterpret_cast<const double2*>(vin);
+  const int h4 = m >> 2;
+  float acc = 0.f;
+  for (int k0 = 0; k0 < h4; k0 += 32 * U) {
+    float4 p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + lane + 32 * u;
+      p[u] = k < h4 ? __ldcs(a + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + lane + 32 * u;
+      if (k < h4) {
+        const double2 x0 = __ldg(v + 2 * k), x1 = __ldg(v + 2 * k + 1);
+        acc = fmaf(p[u].x, (float)x0.x, fmaf(p[u].y, (float)x0.y, fmaf(p[u].z, (float)x1.x, fmaf(p[u].w, (float)x1.y, acc))));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[row] = rs[row] - (double)acc;
+}
+
+// w_t = (D_b^{-1} y_b)_l with FP32 D^{-1} (one warp per row)
+__global__ void __launch_bounds__(256) k_coarse_dinv32(int N, int m, const float* __restrict__ Dinv,
+                                                       const double* __restrict__ y, double* __restrict__ w) {
+  const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (t >= (int64_t)N * m) return;
+  const int64_t b = t / m, l = t - b * m;
+  const float* row = Dinv + (size_t)b * m * m + (size_t)l * m;
+  const double* yb = y + (size_t)b * m;
+  float acc = 0.f;
+  for (int k = lane; k < m; k += 32) acc = fmaf(row[k], (float)yb[k], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) w[t] = (double)acc;
+}
+
+__global__ void k_d2f_blocks(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
 }
 
 __global__ void k_cb_scatter(int64_t rows, const int* __restrict__ perm, const double* __restrict__ xb,
@@ -429,6 +486,21 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense) {
                                                                                                    h->cb_Ut.p));
     h->cb_y.ensure((size_t)N * m);
     h->cb_w.ensure((size_t)N * m);
+    if (h->prec != LAT_FP64 && h->cb_wide) {
+      // the mixed modes apply the FP64 factors as FP32 copies, like the rest of their
+      // preconditioner (the factorisation stays FP64)
+      h->cb_U32.ensure((size_t)N1 * mm);
+      h->cb_Ut32.ensure((size_t)N1 * mm);
+      h->cb_Dinv32.ensure((size_t)N * mm);
+      const int g = 4 * h->n_sm;
+      LAT_LAUNCH(h, k_d2f_blocks<<<g, 256, 0, h->stream>>>((int64_t)N1 * mm, U, h->cb_U32.p));
+      LAT_LAUNCH(h, k_d2f_blocks<<<g, 256, 0, h->stream>>>((int64_t)N1 * mm, h->cb_Ut.p, h->cb_Ut32.p));
+      LAT_LAUNCH(h, k_d2f_blocks<<<g, 256, 0, h->stream>>>((int64_t)N * mm, DE, h->cb_Dinv32.p));
+    } else {
+      h->cb_U32.release();
+      h->cb_Ut32.release();
+      h->cb_Dinv32.release();
+    }
     LAT_CHECK_LAUNCH();
     return;
   }
@@ -534,19 +606,26 @@ void run_coarse_block_solve(lat_ctx* h, const double* g, double* x) {
     h->cb_r.ensure((size_t)rows);
     double *rb = h->cb_r.p, *y = h->cb_y.p, *w = h->cb_w.p;
     const int rb_grid = (int)div_up(rows, 256), st_grid = (int)div_up((int64_t)m * 32, 256);
+    const bool f32 = h->cb_U32.p != nullptr;
+    auto step = [&](const double* M64, const float* M32, const double* vin, const double* rs, double* out) {
+      if (f32) LAT_LAUNCH(h, k_cb_step32<<<st_grid, 256, 0, h->stream>>>(m, M32, vin, rs, out));
+      else LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, M64, vin, rs, out));
+    };
     LAT_LAUNCH(h, k_cb_rhs<<<rb_grid, 256, 0, h->stream>>>(rows, h->cb_perm.p, g, rb));
     LAT_CUDA(cudaMemcpyAsync(y, rb, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     for (int b = 1; b < N; ++b)
-      LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, h->cb_Ut.p + (size_t)(b - 1) * mm,
-                                                              y + (size_t)(b - 1) * m, rb + (size_t)b * m,
-                                                              y + (size_t)b * m));
-    LAT_LAUNCH(h, k_coarse_dinv<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv.p, y, w));
+      step(h->cb_Ut.p + (size_t)(b - 1) * mm, h->cb_Ut32.p + (size_t)(b - 1) * mm, y + (size_t)(b - 1) * m,
+           rb + (size_t)b * m, y + (size_t)b * m);
+    if (f32)
+      LAT_LAUNCH(h, k_coarse_dinv32<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv32.p, y, w));
+    else
+      LAT_LAUNCH(h, k_coarse_dinv<<<div_up(rows * 32, 256), 256, 0, h->stream>>>(N, m, h->cb_Dinv.p, y, w));
     double* xb = rb;   // the right-hand sides are consumed
     LAT_CUDA(cudaMemcpyAsync(xb + (size_t)(N - 1) * m, w + (size_t)(N - 1) * m, m * sizeof(double),
                              cudaMemcpyDeviceToDevice, h->stream));
     for (int b = N - 2; b >= 0; --b)
-      LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, h->cb_U.p + (size_t)b * mm, xb + (size_t)(b + 1) * m,
-                                                              w + (size_t)b * m, xb + (size_t)b * m));
+      step(h->cb_U.p + (size_t)b * mm, h->cb_U32.p + (size_t)b * mm, xb + (size_t)(b + 1) * m, w + (size_t)b * m,
+           xb + (size_t)b * m);
     LAT_LAUNCH(h, k_cb_scatter<<<rb_grid, 256, 0, h->stream>>>(rows, h->cb_perm.p, xb, x));
     LAT_CHECK_LAUNCH();
     return;

@@ -141,6 +141,7 @@ struct lat_ctx {
   std::vector<int32_t> h_cell_layer;
   DBuf<double> cb_A, cb_B, cb_Dinv, cb_Einv, cb_U, cb_V, cb_T, cb_X;
   DBuf<double> cb_Ut, cb_y, cb_w, cb_r; // block-LU solves: U_i^T, forward result, D^-1 y, rhs / x
+  DBuf<float> cb_U32, cb_Ut32, cb_Dinv32; // FP32 copies of the factors (mixed modes, whole-GPU steps)
 
   // selection state
   int n_r = 0;
@@ -191,6 +192,7 @@ struct lat_ctx {
   DBuf<float> CoarseInv32;             // FP32 copy of the coarse inverse (mixed modes)
   int64_t coarse32_ld = 0;             // its row stride (a multiple of 4)
   DBuf<double> tP, gP, xP;            // per-cell primal buffer [n_P][n_cells], primal vectors
+  DBuf<float> tP32, Phi32;            // FP32 per-cell primal buffer and Phi copy (mixed modes)
   DBuf<float> x32, y32;               // mixed-precision local vectors
   DBuf<double> kv_tmp[6];             // saddle-point sized temporaries
   DBuf<double> pcg_ws;                // interface PCG vectors (5 x n_lambda)
@@ -201,6 +203,8 @@ struct lat_ctx {
   DBuf<int> flag;
   DBuf<double> red_part;            // reduction scratch
   int max_tiles = 0;
+  DBuf<int> tile_seg_tc, tile_c0_tc;  // key segments in tiles of kTcCells cells (tensor-core products)
+  int max_tiles_tc = 0;
   bool indefinite = false;              // a principal's remaining block had a negative pivot
   bool coarse_indefinite = false;       // the coarse matrix had a negative pivot
   int64_t pcg_its_total = 0;            // interface PCG iterations since the last reset
@@ -416,6 +420,7 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
 bool coarse_block_plan(lat_ctx* h);
 constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
 constexpr int kWideSweepRows = 512;           // block-LU steps of larger blocks run over the whole GPU
+constexpr int kTcCells = 128;                 // cells per tensor-core tile (the MMA's N)
 void run_coarse_block_solve(lat_ctx* h, const double* g, double* x);
 void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)

@@ -795,27 +795,46 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Y_R^s += Phi^{slot(s)} xP(corners of s)
-__global__ void k_phi_n(int n_cells, int n_K, int n_P, int64_t kstride, const double* __restrict__ Phi,
-                        const int* __restrict__ slot, const int* __restrict__ rdofs, const int* __restrict__ pidx,
-                        const double* __restrict__ xP, const uint8_t* __restrict__ fixed,
-                        const int* __restrict__ pdofs, double* __restrict__ Y) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (s >= n_cells) return;
-  if (i >= n_K) {   // rows n_K.. of the grid clear the corner rows (their values went to g_P)
-    Y[(size_t)pdofs[i - n_K] * n_cells + s] = 0.0;
-    return;
-  }
-  const double* ph = Phi + (size_t)slot[s] * kstride + (size_t)i * n_P;
-  double v = 0;
-  for (int j = 0; j < n_P; ++j) {
-    const int p = pidx[(size_t)s * n_P + j];
-    if (p >= 0) v += ph[j] * xP[p];
-  }
-  const size_t e = (size_t)rdofs[i] * n_cells + s;
-  Y[e] = fixed[e] ? 0.0 : Y[e] + v;
+// corner values of every cell from the primal vector: tP[j][s] = xP[pidx[s][j]] (0 for a
+// Dirichlet primal DOF), in the precision of the product that follows
+template <typename T>
+__global__ void k_gather_tp(int n_cells, int n_P, const int* __restrict__ pidx, const double* __restrict__ xP,
+                            T* __restrict__ tP) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_cells * n_P) return;
+  const int s = (int)(t / n_P), j = (int)(t - (int64_t)s * n_P);
+  const int p = pidx[t];
+  tP[(size_t)j * n_cells + s] = p >= 0 ? (T)xP[p] : T(0);
 }
+
+// Y_R^s += Phi^{slot(s)} tP[:, s] on rows [RB y, RB (y + 1)) of the view (a thread per cell: the
+// cell's corner values are coalesced reads that stay in L1 across the RB rows, Phi rows are
+// broadcast within a warp of cells of one key); rows n_K.. of the grid clear the corner rows
+// (their values went to g_P).  T = FP32 in the mixed modes (an FP32 copy of Phi, part of their
+// FP32 preconditioner).
+template <typename T>
+__global__ void __launch_bounds__(128)
+    k_phi_rows(int n_cells, int n_K, int n_P, int RB, int64_t kstride, const T* __restrict__ Phi,
+               const int* __restrict__ slot, const int* __restrict__ rdofs, const T* __restrict__ tP,
+               const uint8_t* __restrict__ fixed, const int* __restrict__ pdofs, double* __restrict__ Y) {
+  const int s = blockIdx.x * 128 + threadIdx.x;
+  if (s >= n_cells) return;
+  const T* tp = tP + s;
+  const int i0 = blockIdx.y * RB, i1 = min(i0 + RB, n_K + n_P);
+  const T* phs = Phi + (size_t)slot[s] * kstride;
+  for (int i = i0; i < i1; ++i) {
+    if (i >= n_K) {
+      Y[(size_t)pdofs[i - n_K] * n_cells + s] = 0.0;
+      continue;
+    }
+    const T* ph = phs + (size_t)i * n_P;
+    T v = 0;
+    for (int j = 0; j < n_P; ++j) v = fma(ph[j], tp[(size_t)j * n_cells], v);
+    const size_t e = (size_t)rdofs[i] * n_cells + s;
+    Y[e] = fixed[e] ? 0.0 : Y[e] + (double)v;
+  }
+}
+
 
 // y = A x for a dense row-major matrix (warp per row)
 __global__ void k_gemv(int64_t n, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
@@ -1085,6 +1104,17 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_gl
   h->tile_seg.upload(tseg, h->stream);
   h->tile_c0.upload(tc0, h->stream);
   h->max_tiles = (int)tseg.size();
+  if (h->prec == LAT_MIXED_BF16) {
+    std::vector<int> tseg_tc, tc0_tc;
+    for (int k = 0; k < nk; ++k)
+      for (int c = cnt[k]; c < cnt[k + 1]; c += kTcCells) {
+        tseg_tc.push_back(k);
+        tc0_tc.push_back(c);
+      }
+    h->tile_seg_tc.upload(tseg_tc, h->stream);
+    h->tile_c0_tc.upload(tc0_tc, h->stream);
+    h->max_tiles_tc = (int)tseg_tc.size();
+  }
   h->key_slot.upload(slot_cell, h->stream);  // slot of each cell
   // dense local blocks
   const int64_t gstride = (int64_t)(nR + nP) * nR;   // augmented [G; Phi^T] per key
@@ -1160,6 +1190,9 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_gl
   if (h->prec != LAT_FP64) {
     h->G32.ensure(gsz);
     LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, gsz), 256, 0, h->stream>>>(gsz, h->G.p, h->G32.p));
+    const size_t psz = (size_t)nk * nR * nP;
+    h->Phi32.ensure(std::max<size_t>(1, psz));
+    LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, std::max<size_t>(1, psz)), 256, 0, h->stream>>>(psz, h->Phi.p, h->Phi32.p));
     const size_t dsz = (size_t)nk * nD * nD;
     h->SDD32.ensure(dsz);
     LAT_LAUNCH(h, k_d2f<<<ew_blocks(h, dsz), 256, 0, h->stream>>>(dsz, h->SDD.p, h->SDD32.p));
@@ -1304,9 +1337,26 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
     run_coarse_solve(h, h->gP.p, pr_of(h, w));
   }
   if (h->n_primal) {
-    // w_R += Phi x_P on the view's rows; the extra nP grid rows clear the corner rows
-    LAT_LAUNCH(h, k_phi_n<<<dim3(div_up(ns, 128), nKr + nP), 128, 0, h->stream>>>(ns, nKr, nP, (int64_t)nR * nP,
-        h->Phi.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->pidx.p, pr_of(h, w), h->loc_fixed.p, h->pdofs.p, wl));
+    // w_R += Phi x_P on the view's rows (corner values gathered per cell first); the extra nP
+    // rows clear the corner rows
+    constexpr int RB = 32;
+    const dim3 grid(div_up(ns, 128), div_up(nKr + nP, RB));
+    const int64_t gt = (int64_t)ns * nP;
+    if (lo && h->Phi32.p) {
+      h->tP32.ensure((size_t)gt);
+      LAT_LAUNCH(h, k_gather_tp<float><<<div_up(gt, 256), 256, 0, h->stream>>>(ns, nP, h->pidx.p, pr_of(h, w),
+                                                                               h->tP32.p));
+      LAT_LAUNCH(h, k_phi_rows<float><<<grid, 128, 0, h->stream>>>(
+          ns, nKr, nP, RB, (int64_t)nR * nP, h->Phi32.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->tP32.p,
+          h->loc_fixed.p, h->pdofs.p, wl));
+    } else {
+      h->tP.ensure((size_t)gt);
+      LAT_LAUNCH(h, k_gather_tp<double><<<div_up(gt, 256), 256, 0, h->stream>>>(ns, nP, h->pidx.p, pr_of(h, w),
+                                                                                h->tP.p));
+      LAT_LAUNCH(h, k_phi_rows<double><<<grid, 128, 0, h->stream>>>(
+          ns, nKr, nP, RB, (int64_t)nR * nP, h->Phi.p + (size_t)lo_r * nP, h->key_slot.p, rr, h->tP.p,
+          h->loc_fixed.p, h->pdofs.p, wl));
+    }
     LAT_CHECK_LAUNCH();
   } else {
     LAT_LAUNCH(h, k_zero_rows<<<div_up(ns, 256), 256, 0, h->stream>>>(ns, nP, h->pdofs.p, wl));

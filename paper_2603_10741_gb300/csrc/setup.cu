@@ -353,10 +353,11 @@ void build_feti_impl(lat_ctx* h, int level) {
   h->p_copy.upload(pc, h->stream);
 
   // multipliers: each free non-corner DOF with m copies gets m-1 multipliers joining
-  // consecutive copies in cell order (non-redundant)
-  std::vector<int> lp, lm;
-  std::map<int, std::pair<int, int>> dual;  // local entry -> (l1, l2) signed (l+1)
-  std::map<int, double> dscale;
+  // consecutive copies in cell order (non-redundant).  They are numbered in the order of their
+  // first copy's cell-stacked entry (local DOF major, cell minor), so that the jump kernels, which
+  // walk the dual entries in that order, read the multiplier vector nearly contiguously.
+  std::vector<std::pair<int, int>> pairs;   // (entry of the + copy, entry of the - copy)
+  std::map<int, int> mult;                  // dual entry -> multiplicity of its node
   for (int64_t g = 0; g < h->n_glob_nodes; ++g) {
     int m = cptr[g + 1] - cptr[g];
     if (m < 2) continue;
@@ -368,18 +369,27 @@ void build_feti_impl(lat_ctx* h, int level) {
         int ca = cidx[cptr[g] + c], cb = cidx[cptr[g] + c + 1];
         int ea = ((ca % nn) * d + i) * ns + ca / nn;
         int eb = ((cb % nn) * d + i) * ns + cb / nn;
-        int l = (int)lp.size();
-        lp.push_back(ea);
-        lm.push_back(eb);
-        auto put = [&](int e, int v) {
-          auto& pr = dual[e];
-          if (pr.first == 0) pr.first = v; else pr.second = v;
-          dscale[e] = 1.0 / m;
-        };
-        put(ea, l + 1);
-        put(eb, -(l + 1));
+        pairs.push_back({ea, eb});
+        mult[ea] = m;
+        mult[eb] = m;
       }
     }
+  }
+  std::sort(pairs.begin(), pairs.end());
+  std::vector<int> lp, lm;
+  std::map<int, std::pair<int, int>> dual;  // local entry -> (l1, l2) signed (l+1)
+  std::map<int, double> dscale;
+  for (const auto& pr2 : pairs) {
+    const int l = (int)lp.size();
+    lp.push_back(pr2.first);
+    lm.push_back(pr2.second);
+    auto put = [&](int e, int v) {
+      auto& pr = dual[e];
+      if (pr.first == 0) pr.first = v; else pr.second = v;
+      dscale[e] = 1.0 / mult[e];
+    };
+    put(pr2.first, l + 1);
+    put(pr2.second, -(l + 1));
   }
   h->n_lambda = (int64_t)lp.size();
   h->lam_p.upload(lp, h->stream);
@@ -459,8 +469,9 @@ void build_feti_impl(lat_ctx* h, int level) {
     };
     Blocking hi = blocking(true), lo = blocking(false);
     const Blocking& B = lo.m < hi.m ? lo : hi;
-    // blocks padded to an even size (identity on the padding): 16-byte rows for the sweeps
-    const int N = B.N, m = (B.m + 1) & ~1;
+    // blocks padded to a multiple of 4 (identity on the padding): 16-byte rows for the sweeps
+    // in FP64 and FP32
+    const int N = B.N, m = (B.m + 3) & ~3;
     bool tri = N >= 2;
     std::vector<int64_t> dest(crow.size(), -1);
     const size_t mm = (size_t)m * m;
@@ -604,7 +615,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->f_cells); rel(h->r_glob); rel(h->minJ_cell); rel(h->T); rel(h->negJ);
   rel(h->key_of_cell); rel(h->key_slot); rel(h->perm); rel(h->seg_ptr); rel(h->tile_seg);
   rel(h->tile_c0); rel(h->key_list); rel(h->solver_int); rel(h->delta_cell); rel(h->c_cell);
-  rel(h->G); rel(h->G16[0]); rel(h->G16[1]); rel(h->G16[2]); rel(h->G16[3]); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->KRP); rel(h->Coarse);
+  rel(h->G); rel(h->G16[0]); rel(h->G16[1]); rel(h->G16[2]); rel(h->G16[3]); rel(h->cb_U32); rel(h->cb_Ut32); rel(h->cb_Dinv32); rel(h->tile_seg_tc); rel(h->tile_c0_tc); rel(h->tP32); rel(h->Phi32); rel(h->SDD); rel(h->SDD32); rel(h->Phi); rel(h->Sloc); rel(h->G32); rel(h->Xb16); rel(h->KRP); rel(h->Coarse);
   rel(h->CoarseInv); rel(h->CoarseInv32); rel(h->pcg_ws); rel(h->tP); rel(h->gP); rel(h->xP); rel(h->x32); rel(h->y32);
   for (auto& b : h->kv_tmp) rel(b);
   rel(h->V); rel(h->Zk); rel(h->Hh); rel(h->gmres_small); rel(h->dots_part); rel(h->flag); rel(h->red_part);

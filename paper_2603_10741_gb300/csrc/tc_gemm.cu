@@ -2,7 +2,7 @@
 // BF16 mixed mode: the local part of K^-rom (Eq. ifetidp_precond, Section 3.3.1) for all cells,
 //   Y[rows of cell s] = [G; Phi^T]_{key(s)} X_R^s,   G = (K_RR^r)^{-1} of the cell's principal,
 // as a segmented GEMM over cells grouped by key: one CTA computes MW tiles of 128 rows x TN
-// cells of one key (TN = 64, MW = 1 in use) with A = rows of the key's augmented matrix and
+// cells of one key (TN = 128, MW = 1 in use) with A = rows of the key's augmented matrix and
 // B = the cells' remaining values, accumulating
 // in FP32 in tensor memory.  Each operand is a BF16 pair (high part and the BF16 rounding of the
 // remainder) and three products G_hi X_hi + G_hi X_lo + G_lo X_hi accumulate into the same
@@ -19,7 +19,9 @@
 // on an mbarrier with their byte count).  One elected thread issues
 // the copies and the MMAs (M = 128, N = TN, K = 16 per instruction), commits each stage's MMAs
 // to that stage's "empty" barrier before refilling it, and a final commit releases the
-// epilogue.  Three stages are in flight for MW = 1 (four for MW = 2).  Every wait is bounded: on a timeout the kernel flags an error, gives outstanding
+// epilogue.  A stage carries one K panel of both BF16 halves of A and of B (64 KiB for TN =
+// 128), so the three products of the panel cost one load of each operand; three stages are in
+// flight.  Every wait is bounded: on a timeout the kernel flags an error, gives outstanding
 // work a bounded chance to finish, frees its tensor memory and returns.
 #include "common.cuh"
 
@@ -38,8 +40,10 @@ template <int TN, int MW>
 struct TcCfg {
   static constexpr int B_ELEMS = TN * TK;
   static constexpr int B_BYTES = B_ELEMS * 2;
-  static constexpr int STAGE_BYTES = MW * A_BYTES + B_BYTES;
-  static constexpr int STAGES = MW == 1 ? 3 : 4;   // 72 KiB (three CTAs per SM) or 192 KiB
+  // a stage holds one K panel of both BF16 halves of A (MW tiles) and of B: the three products
+  // of the panel are issued from one load
+  static constexpr int STAGE_BYTES = 2 * (MW * A_BYTES + B_BYTES);
+  static constexpr int STAGES = 3;   // TN = 128: 3 x 64 KiB
   static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES;
   static constexpr int TMEM_COLS = MW * TN;   // MW accumulators of TN FP32 columns
   // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4
@@ -105,8 +109,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 // the last CTA of a key may have one) times the TN cells of tile `tile` (key-ordered positions
 // [c0, c0 + TN)).  GT: tiled high parts [key][mt][kp][8192] (low parts lo_off elements later),
 // XT: tiled cell vectors [tile][2 KP][TN x 64] (high panels 0..KP-1, low panels KP..2KP-1).
-// Panel p of the 3 KP panels is (pass, kp) = (p / KP, p % KP): passes G_hi X_hi, G_hi X_lo,
-// G_lo X_hi.  With MW = 2 every B panel feeds two M tiles (two accumulators in tensor memory).
+// Stage p holds K panel p of G_hi, G_lo, X_hi and X_lo; the products G_hi X_hi, G_hi X_lo and
+// G_lo X_hi of the panel accumulate into the same tensor-memory tile.  With MW = 2 every B panel
+// feeds two M tiles (two accumulators in tensor memory).
 template <int TN, int MW>
 __global__ void __launch_bounds__(128)
     k_local_tc(int n_cells, int n_Kr, int n_P, int MT, int KP, int64_t lo_off, const __nv_bfloat16* __restrict__ GT,
@@ -127,24 +132,27 @@ __global__ void __launch_bounds__(128)
   const int c0 = tile_c0[tile];
   const int c_end = seg_ptr[key + 1];
   const int rows = n_Kr + n_P;
-  const int P2 = 3 * KP;
-  const uint32_t stage_tx = (uint32_t)(nm * A_BYTES + C::B_BYTES);
+  const int P2 = KP;
+  const uint32_t stage_tx = (uint32_t)(2 * (nm * A_BYTES + C::B_BYTES));
   const uint32_t s0 = smem_u32(smem);
-  auto sA = [&](int st, int m) { return s0 + (uint32_t)(st * C::STAGE_BYTES + m * A_BYTES); };
-  auto sB = [&](int st) { return s0 + (uint32_t)(st * C::STAGE_BYTES + MW * A_BYTES); };
-  auto gA = [&](int p, int m) {
-    const int pass = p / KP, kp = p - pass * KP;
-    return (const void*)(GT + (((size_t)key * MT + mt0 + m) * KP + kp) * A_ELEMS + (pass == 2 ? lo_off : 0));
+  // stage layout: [A_hi tiles | A_lo tiles | B_hi | B_lo]
+  auto sA = [&](int st, int m, int half) {
+    return s0 + (uint32_t)(st * C::STAGE_BYTES + (half * MW + m) * A_BYTES);
   };
-  auto gB = [&](int p) {
-    const int pass = p / KP, kp = p - pass * KP;
-    return (const void*)(XT + ((size_t)tile * 2 * KP + (pass == 1 ? KP + kp : kp)) * C::B_ELEMS);
+  auto sB = [&](int st, int half) { return s0 + (uint32_t)(st * C::STAGE_BYTES + 2 * MW * A_BYTES + half * C::B_BYTES); };
+  auto gA = [&](int kp, int m, int half) {
+    return (const void*)(GT + (((size_t)key * MT + mt0 + m) * KP + kp) * A_ELEMS + (half ? lo_off : 0));
   };
-  auto load = [&](int p, int st) {
+  auto gB = [&](int kp, int half) {
+    return (const void*)(XT + ((size_t)tile * 2 * KP + (half ? KP + kp : kp)) * C::B_ELEMS);
+  };
+  auto load = [&](int kp, int st) {
     const uint32_t bar = smem_u32(&full[st]);
     expect_tx(bar, stage_tx);
-    for (int m = 0; m < nm; ++m) bulk_copy(sA(st, m), gA(p, m), (uint32_t)A_BYTES, bar);
-    bulk_copy(sB(st), gB(p), (uint32_t)C::B_BYTES, bar);
+    for (int half = 0; half < 2; ++half) {
+      for (int m = 0; m < nm; ++m) bulk_copy(sA(st, m, half), gA(kp, m, half), (uint32_t)A_BYTES, bar);
+      bulk_copy(sB(st, half), gB(kp, half), (uint32_t)C::B_BYTES, bar);
+    }
   };
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
@@ -167,7 +175,9 @@ __global__ void __launch_bounds__(128)
   const uint32_t tmem = tmem_slot;
 
   if (tid == 0) {
-    // producer and MMA issuer in one thread: copies run up to STAGES panels ahead
+    // producer and MMA issuer in one thread: copies run up to STAGES panels ahead.  The stage of
+    // panel p - 1 is refilled after panel p's MMAs are queued, so that the tensor pipe always has
+    // a panel queued while the thread waits for the previous one to drain.
     int issued = 0;
     for (; issued < STAGES && issued < P2; ++issued) load(issued, issued);
     bool ok = true;
@@ -182,25 +192,30 @@ __global__ void __launch_bounds__(128)
       for (int m = 0; m < nm; ++m) {
 #pragma unroll
         for (int ks = 0; ks < TK / KSTEP; ++ks) {
-          const uint64_t ad = make_desc(sA(st, m) + ks * 2 * 128);
-          const uint64_t bd = make_desc(sB(st) + ks * 2 * 128);
-          const uint32_t acc = (p > 0 || ks > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred q;\n\t"
-              "setp.ne.b32 q, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem + (uint32_t)(m * TN)),
-              "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
-              : "memory");
+          // G_hi X_hi, G_hi X_lo, G_lo X_hi (the G_lo X_lo term is below the pairs' precision)
+#pragma unroll
+          for (int pass = 0; pass < 3; ++pass) {
+            const uint64_t ad = make_desc(sA(st, m, pass == 2) + ks * 2 * 128);
+            const uint64_t bd = make_desc(sB(st, pass == 1) + ks * 2 * 128);
+            const uint32_t acc = (p > 0 || ks > 0 || pass > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred q;\n\t"
+                "setp.ne.b32 q, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n\t}" ::"r"(tmem + (uint32_t)(m * TN)),
+                "l"(ad), "l"(bd), "r"(C::IDESC), "r"(acc)
+                : "memory");
+          }
         }
       }
       mma_commit(smem_u32(&empty[st]));
-      if (issued < P2) {
-        // refill this stage once its MMAs have read it
-        if (!mbar_wait(smem_u32(&empty[st]), ph)) {
+      if (p >= 1 && issued < P2) {
+        // refill the previous panel's stage once its MMAs have read it
+        const int sp = (p - 1) % STAGES;
+        if (!mbar_wait(smem_u32(&empty[sp]), (uint32_t)(((p - 1) / STAGES) & 1))) {
           ok = false;
           break;
         }
-        load(issued, st);
+        load(issued, sp);
         ++issued;
       }
     }
@@ -218,12 +233,14 @@ __global__ void __launch_bounds__(128)
   const bool ok = fin && !fail;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (__syncthreads_and(ok ? 1 : 0)) {
-    // epilogue: warp w reads accumulator lanes 32w..32w+31 (tile rows), 16 columns at a time
+    // epilogue: warp w reads accumulator lanes 32w..32w+31 (tile rows), 16 columns at a time,
+    // and writes them through a per-warp transpose tile in the (now idle) pipeline shared memory,
+    // so that the 16 lanes of a half-warp store 16 consecutive cells of one output row
+    float* tb = reinterpret_cast<float*>(smem) + warp * 32 * 17;
+    const int half = lane >> 4, j16 = lane & 15;
     for (int m = 0; m < nm; ++m) {
-      const int gi = (mt0 + m) * TM + warp * 32 + lane;
-      const bool row_ok = gi < rows;
-      const size_t orow = row_ok ? (size_t)(gi < n_Kr ? rr[gi] : pdofs[gi - n_Kr]) : 0;
-#pragma unroll
+      const int row0 = (mt0 + m) * TM + warp * 32;
+#pragma unroll 1
       for (int cb = 0; cb < TN; cb += 16) {
         uint32_t r[16];
         const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * TN + cb);
@@ -235,16 +252,26 @@ __global__ void __launch_bounds__(128)
             : "r"(taddr)
             : "memory");
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row_ok) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int pos = c0 + cb + j;
-            if (pos >= c_end) continue;
-            const int s = perm[pos];
-            const double v = (double)__uint_as_float(r[j]);
-            Y[orow * n_cells + s] = gi < n_Kr ? (mul_scale ? v * cscale[s] : v / cscale[s]) : v;
+        for (int j = 0; j < 16; ++j) tb[lane * 17 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int pos = c0 + cb + j16;
+        const bool col_ok = pos < c_end;
+        const int s = col_ok ? perm[pos] : 0;
+        // the cell's factor c_s (S_DD rows) or 1 / c_s (G rows), one division per column
+        const double cs = col_ok ? cscale[s] : 1.0;
+        const double fac = mul_scale ? cs : 1.0 / cs;
+#pragma unroll 4
+        for (int q = 0; q < 16; ++q) {
+          const int rl = 2 * q + half;
+          const int gi = row0 + rl;
+          if (col_ok && gi < rows) {
+            const size_t orow = (size_t)(gi < n_Kr ? rr[gi] : pdofs[gi - n_Kr]);
+            const double v = (double)tb[rl * 17 + j16];
+            Y[orow * n_cells + s] = gi < n_Kr ? v * fac : v;
           }
         }
+        __syncwarp();
       }
     }
   } else if (tid == 0) {
@@ -384,28 +411,26 @@ void launch_sdd_tc(lat_ctx* h, const double* X, double* Y) {
   const int KP = h->g16_ld[3];
   const int* rd = h->rdofs.p + h->n_I;
   const int KPmax = std::max(1, div_up(h->n_R, TK));
-  h->Xb16.ensure((size_t)h->max_tiles * 2 * KPmax * C::B_ELEMS);
-  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(h->max_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nD, KP, X, h->tile_seg.p,
-                                                                              h->tile_c0.p, h->seg_ptr.p, h->perm.p,
+  h->Xb16.ensure((size_t)h->max_tiles_tc * 2 * KPmax * C::B_ELEMS);
+  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(h->max_tiles_tc, KP), 256, 0, h->stream>>>(h->n_cells, nD, KP, X, h->tile_seg_tc.p,
+                                                                              h->tile_c0_tc.p, h->seg_ptr.p, h->perm.p,
                                                                               rd, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc<TN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM_BYTES));
-  dim3 grid(h->max_tiles, MT);
+  dim3 grid(h->max_tiles_tc, MT);
   KernelTimer kt(h, "dual_schur_tc");
   LAT_LAUNCH(h, (k_local_tc<TN, 1><<<grid, 128, C::SMEM_BYTES, h->stream>>>(
-                    h->n_cells, nD, 0, MT, KP, h->g16_lo[3], h->G16[3].p, h->Xb16.p, h->tile_seg.p, h->tile_c0.p,
+                    h->n_cells, nD, 0, MT, KP, h->g16_lo[3], h->G16[3].p, h->Xb16.p, h->tile_seg_tc.p, h->tile_c0_tc.p,
                     h->seg_ptr.p, h->perm.p, h->c_cell.p, rd, h->pdofs.p, Y, h->flag.p, 1)));
   LAT_CHECK_LAUNCH();
 }
 
 }  // namespace
 
-// Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores, on the
-// 64-cell tiles of the mixed modes' segmented products, three CTAs per SM.  (128-cell tiles with
-// two M tiles per CTA halve the operand traffic per multiply-add but leave SMs idle at the
-// problem sizes here: 99 CTAs for the 10x10x10 strut lattice, measured slower.)
+// Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores, on
+// 128-cell tiles of each key's cells, one CTA per SM.
 void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
-  launch_tc<64, 1>(h, X, Y, mode, h->tile_seg.p, h->tile_c0.p, h->max_tiles);
+  launch_tc<kTcCells, 1>(h, X, Y, mode, h->tile_seg_tc.p, h->tile_c0_tc.p, h->max_tiles_tc);
 }
 
-void run_sdd_tc(lat_ctx* h, const double* X, double* Y) { launch_sdd_tc<64>(h, X, Y); }
+void run_sdd_tc(lat_ctx* h, const double* X, double* Y) { launch_sdd_tc<kTcCells>(h, X, Y); }
