@@ -126,3 +126,29 @@ def tangent(cell: RefCell, u, mu, lam, reduced=False, chunk=64):
 def snapshots(cell: RefCell, u, mu, lam):
     """Snapshot matrix T = [t^1 ... t^Ns], t^s = data(Kbar^s) with the reduced rule: [nnz, nc]."""
     return tangent(cell, u, mu, lam, reduced=True).T.copy()
+
+
+def dref_snapshots(cell: RefCell, u, mu, lam):
+    """Snapshot matrix of the pulled-back tangent tensor (the Remark after Eq. snapshots):
+    t^s = vec({D^ref(xi_q)}) over the one-point rule of every element, [n_el * d^4, nc].
+
+    Eq. (tensorfunctionPulledback) with Psi the map from the element's parameter cube to the
+    current configuration, J = dx/dxi = F J0 (J0 = dX/dxi of the reference cell):
+        D^ref_ijmn = sum_kl D_ijkl (J^-1)_mk (J^-1)_nl |det J|,
+    so that [K_ab]_ij = sum_q w_q sum_mn D^ref_ijmn dphi_a/dxi_m dphi_b/dxi_n (Eq.
+    stiffmatPulledback).  Entries ordered (element, i, j, m, n), last fastest."""
+    d = cell.d
+    xi, _ = fe.gauss_rule(1, d)
+    gref = fe.q1_grad_ref(xi)                                     # [1, nen, d]
+    Xe = cell.X[cell.elems]                                       # [ne, nen, d]
+    J0 = np.einsum("eak,qal->eqkl", Xe, gref)                     # [ne, 1, d, d]
+    F = deformation_gradient(cell, u, reduced=True)               # [nc, ne, 1, d, d]
+    Jm = np.einsum("ceqkp,eqpl->ceqkl", F, J0)                    # dx_k / dxi_l
+    if np.any(np.linalg.det(F) <= 0):
+        raise FloatingPointError("non-positive Jacobian")
+    Jinv = np.linalg.inv(Jm)                                      # dxi_m / dx_k
+    detJ = np.abs(np.linalg.det(Jm))
+    mu_b = np.broadcast_to(np.asarray(mu, dtype=float)[:, None, None], detJ.shape)
+    D = tangent_tensor_D(F, mu_b, lam)                            # [nc, ne, 1, d, d, d, d]
+    Dref = np.einsum("ceqijkl,ceqmk,ceqnl,ceq->ceqijmn", D, Jinv, Jinv, detJ)
+    return Dref.reshape(u.shape[0], -1).T.copy()

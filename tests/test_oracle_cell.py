@@ -173,3 +173,52 @@ def test_one_point_rule_matches_closed_form_on_a_skewed_element(d):
     assert np.abs(K2 - ref).max() > 1e-2 * np.abs(ref).max()
     # one point sees only the centre strain: the rank is the number of strain components
     assert np.linalg.matrix_rank(K1, tol=1e-10 * np.abs(K1).max()) == (3 if d == 2 else 6)
+
+
+@pytest.mark.parametrize("which", ["ring", "strut"])
+def test_dref_snapshot_reassembles_the_reduced_rule_tangent(which):
+    """The D^ref snapshot (pulled-back tangent tensor at the one-point rule, Eq.
+    tensorfunctionPulledback) contracted with the reference gradients of the Q1 element at its
+    centre, times the one-point weight 2^d, gives back the reduced-rule tangent computed through
+    the current-configuration gradients (Eq. stiffmatPulledback): a check of the pull-back's
+    index placement and Jacobian factor against an independent path."""
+    X, E = latgen.ring_cell(4) if which == "ring" else latgen.strut_cell(4, 0.3)
+    cell = C.RefCell(X, E)
+    d = cell.d
+    rng = np.random.default_rng(7)
+    u = 0.02 * rng.uniform(-1, 1, (2, cell.n_nodes, d))
+    mu = np.array([1.1, 0.9])
+    T = C.dref_snapshots(cell, u, mu, 4.0)
+    assert T.shape == (cell.n_el * d ** 4, 2)
+    Kbar = C.tangent(cell, u, mu, 4.0, reduced=True)
+    corners = _q1_corners(d)
+    g0 = corners / 2 ** d                                  # dphi_a / dxi at the element centre
+    for s in range(2):
+        Dref = T[:, s].reshape(cell.n_el, d, d, d, d)
+        K = np.zeros((cell.n_nodes * d, cell.n_nodes * d))
+        for e, el in enumerate(cell.elems):
+            Ke = 2 ** d * np.einsum("ijmn,am,bn->aibj", Dref[e], g0, g0)
+            for a, na in enumerate(el):
+                for b, nb in enumerate(el):
+                    K[na * d:(na + 1) * d, nb * d:(nb + 1) * d] += Ke[a, :, b, :]
+        ref = cell.dense(Kbar[s])
+        assert np.abs(K - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_dref_snapshot_at_rest_is_the_pulled_back_elasticity():
+    """At rest on an axis-aligned element of side h (J = (h/2) I): D^ref_ijmn = C_imjn (2/h)^2
+    (h/2)^d with C_ikjl = lam d_ik d_jl + mu (d_ij d_kl + d_il d_kj) (no stress, J = 1)."""
+    d, h, mu, lam = 3, 0.5, 1.3, 4.0
+    X, E = latgen.solid_cell(1, d)
+    cell = C.RefCell(X * h, np.asarray(E))
+    T = C.dref_snapshots(cell, np.zeros((1, cell.n_nodes, d)), np.array([mu]), lam)
+    Dref = T[:, 0].reshape(d, d, d, d)
+    dl = np.eye(d)
+    ref = np.zeros((d, d, d, d))
+    for i in range(d):
+        for j in range(d):
+            for m in range(d):
+                for n in range(d):
+                    ref[i, j, m, n] = lam * dl[i, m] * dl[j, n] + mu * (dl[i, j] * dl[m, n] + dl[i, n] * dl[m, j])
+    ref *= (2 / h) ** 2 * (h / 2) ** d
+    assert np.abs(Dref - ref).max() < 1e-13 * np.abs(ref).max()
