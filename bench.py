@@ -71,6 +71,9 @@ def parse():
     p.add_argument("--quick", action="store_true", help="skip the plain-path comparison and the extras")
     p.add_argument("--detail", default=None, help="write the full breakdown as JSON to this path")
     p.add_argument("--sample-cells", type=int, default=512, help="cells in the oracle's bounded sample")
+    p.add_argument("--profile-step", action="store_true",
+                   help="bracket one more Newton iteration (after the timed region) with cudaProfilerStart/Stop, "
+                        "for a profiler started with --profile-from-start off")
     args = p.parse_args()
     if args.precision is None:
         args.precision = DEFAULT_PRECISION[args.case]
@@ -406,6 +409,13 @@ def run_ours(args):
     value = ws * stacked * n_apply / apply_s / 1e9 if n_apply else 0.0
     n_launch = count_launches(lat, opts, u_start)
 
+    if args.profile_step:
+        u.copy_(u_start)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        lat.newton_step(u, opts, max_iterations=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     # per-kernel breakdown of one more iteration (every named kernel timed)
     lat.lattice_set_timing(1)
     u.copy_(u_start)

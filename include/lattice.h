@@ -174,6 +174,13 @@ lat_status select_principal_cells(lat_handle h, const double* u_glob, double eps
                                   int32_t force_all, int32_t* S, int32_t* n_r, double* alpha,
                                   double* K_p);
 
+/* Snapshot kind of select_principal_cells (newton_step and adjoint_gradient take it from their
+ * options): 0 the reduced-rule local tangents' data (Eq. snapshots), 1 the pulled-back tangent
+ * tensor D^ref_ijmn = |det J| sum_kl D_ijkl (J^-1)_mk (J^-1)_nl, J = dx/dxi = F J0, at the
+ * one-point rule of every element (Eq. tensorfunctionPulledback, the Remark after Eq.
+ * snapshots), entries ordered (element, i, j, m, n).  LAT_EINVAL for another kind. */
+lat_status lattice_set_snapshots(lat_handle h, int32_t kind);
+
 /* Caller-given principal set for the reduced tangent action (Eq. romstiffnessmatrix with S and
  * alpha chosen by the caller instead of by Algorithm 1; the paper has no such entry point, its
  * principal set always comes from the greedy).  u_glob (dev, FP64 [n_dof]): state at which the
@@ -235,6 +242,11 @@ typedef struct {
                               the FP64 reduced tangent.  0: the block preconditioner directly.
                               Ignored in LAT_FP64 */
   double inner_rtol;       /* inner GMRES stops early at this relative residual */
+  int32_t snapshot;        /* snapshots fed to Algorithm 1: 0 (default) the data of the
+                              reduced-rule local tangents (Eq. snapshots), 1 the pulled-back
+                              tangent tensor D^ref (Eq. tensorfunctionPulledback) at the
+                              one-point rule of every element (the Remark after Eq. snapshots:
+                              n_el d^4 values per cell instead of nnz) */
 } lat_newton_opts;
 
 typedef struct {

@@ -234,6 +234,124 @@ __global__ void __launch_bounds__(kCellThreads)
 }
 
 // ---------------------------------------------------------------------------------------------
+// D^ref snapshots (the Remark after Eq. snapshots): the pulled-back tangent tensor of Eq.
+// (tensorfunctionPulledback) at the one-point rule of every element,
+//   D^ref_ijmn = |det J| sum_kl D_ijkl G_mk G_nl,   G = J^{-1}, J = dx/dxi = F J0,
+//   D_ijkl = C_ikjl + delta_ij sigma_kl  (Eq. const_eq, Section 3.1.4), which expands to
+//   D^ref_ijmn = |det J| [lam/J G_mi G_nj + c (delta_ij (G G^T)_mn + G_mj G_ni)
+//                         + delta_ij (G sigma G^T)_mn],   c = (mu - lam ln J) / J.
+// J0^{-1} follows from the reference gradients at the centre: the Q1 corner signs xi_a satisfy
+// sum_a xi_a,m xi_a,m' = 2^d delta, so (J0^{-1})_mk = sum_a xi_a,m dphi_a/dX_k.  A thread per
+// (cell, element); output [n_cells][n_el * d^4], entries (element, i, j, m, n) last fastest.
+// ---------------------------------------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(128)
+    k_dref(int n_cells, int n_el, int nn, GeomArgs g, const int* __restrict__ cell_nodes,
+           const double* __restrict__ mu_cell, double lam, const double* __restrict__ u_glob,
+           double* __restrict__ T, double* __restrict__ minJ_cell) {
+  constexpr int NEN = 1 << D;
+  constexpr int D4 = D * D * D * D;
+  const int s = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double red[32];
+  double myJ = DBL_MAX;
+  if (e < n_el) {
+    const int* cn = cell_nodes + (size_t)s * nn;
+    const double* gq = g.gradX + (size_t)e * NEN * D;   // one point per element
+    double F[D][D], Fi[D][D], Ji0[D][D];
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        F[i][k] = (i == k) ? 1.0 : 0.0;
+        Ji0[i][k] = 0.0;
+      }
+#pragma unroll
+    for (int a = 0; a < NEN; ++a) {
+      const int node = g.elems[e * NEN + a];
+      const int64_t gn = cn[node];
+      // Q1 corner a in the counter-clockwise / bottom-then-top order: signs of xi_a
+      const double sx = ((a & 3) == 1 || (a & 3) == 2) ? 1.0 : -1.0;
+      const double sy = ((a & 3) >= 2) ? 1.0 : -1.0;
+      const double sz = a >= 4 ? 1.0 : -1.0;
+      const double sg[3] = {sx, sy, sz};
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        const double ui = u_glob[gn * D + i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) F[i][k] += ui * gq[a * D + k];
+      }
+#pragma unroll
+      for (int m = 0; m < D; ++m)
+#pragma unroll
+        for (int k = 0; k < D; ++k) Ji0[m][k] += sg[m] * gq[a * D + k];
+    }
+    const double J = det_inv<D>(F, Fi);
+    myJ = J;
+    const double lnJ = J > 0 ? log(J) : 0.0;
+    const double mu = mu_cell[s];
+    const double detJ0 = g.W[e] / (double)(1 << D);         // one-point weight 2^d |det J0|
+    const double dJ = fabs(J) * detJ0;
+    double G[D][D];                                         // J^{-1} = J0^{-1} F^{-1}
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        double v = 0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) v += Ji0[m][p] * Fi[p][k];
+        G[m][k] = v;
+      }
+    double sig[D][D];                                       // Eq. (sig_eq)
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        double b = 0;
+#pragma unroll
+        for (int p = 0; p < D; ++p) b += F[k][p] * F[l][p];
+        sig[k][l] = mu / J * (b - (k == l ? 1.0 : 0.0)) + (k == l ? lam * lnJ / J : 0.0);
+      }
+    double A[D][D], Sg[D][D];
+#pragma unroll
+    for (int m = 0; m < D; ++m)
+#pragma unroll
+      for (int n = 0; n < D; ++n) {
+        double a1 = 0, a2 = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          a1 += G[m][k] * G[n][k];
+          double t = 0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) t += sig[k][l] * G[n][l];
+          a2 += G[m][k] * t;
+        }
+        A[m][n] = a1;
+        Sg[m][n] = a2;
+      }
+    const double cl = lam / J, cc = (mu - lam * lnJ) / J;
+    double* out = T + (size_t)s * n_el * D4 + (size_t)e * D4;
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j)
+#pragma unroll
+        for (int m = 0; m < D; ++m)
+#pragma unroll
+          for (int n = 0; n < D; ++n) {
+            double v = cl * G[m][i] * G[n][j] + cc * G[m][j] * G[n][i];
+            if (i == j) v += cc * A[m][n] + Sg[m][n];
+            out[((i * D + j) * D + m) * D + n] = dJ * v;
+          }
+  }
+  const double mj = -block_max(-myJ, red);
+  if (threadIdx.x == 0 && minJ_cell) {
+    // the CTAs of a cell combine through an atomic-free per-(cell, CTA) slot
+    minJ_cell[(size_t)s * gridDim.x + blockIdx.x] = mj;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // exact tangent action y = K(u) v without storing K (matrix free, full rule):
 //   dP_iK = mu dF_iK + lam tr(F^{-1} dF) F^{-1}_Ki + (mu - lam ln J) (F^{-1} dF F^{-1})_Ki
 // output cell-stacked local forces [n_loc][n_cells]
@@ -470,6 +588,30 @@ void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, i
   if (negJ) {
     double* sc = scratch_scalars(h);
     LAT_LAUNCH(h, k_min_reduce<<<1, 1024, 0, h->stream>>>(n_sel, h->minJ_cell.p, sc));
+    LAT_CHECK_LAUNCH();
+    LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LAT_CUDA(cudaStreamSynchronize(h->stream));
+    *negJ = !(h->h_pinned[0] > 0.0);
+  }
+}
+
+// D^ref snapshots of every cell: T [n_cells][n_el * d^4]
+void run_dref_snapshots(lat_ctx* h, const double* u_glob, double* T, bool* negJ) {
+  const int nb = div_up(h->n_el, 128);
+  h->minJ_cell.ensure((size_t)h->n_cells * nb);
+  auto g = geom(h, 1);
+  const dim3 grid(nb, h->n_cells);
+  KernelTimer kt(h, "dref_snapshots");
+  if (h->dim == 2)
+    LAT_LAUNCH(h, k_dref<2><<<grid, 128, 0, h->stream>>>(h->n_cells, h->n_el, h->n_nodes_cell, g, h->cell_nodes.p,
+                                                          h->mu_cell.p, h->lam, u_glob, T, h->minJ_cell.p));
+  else
+    LAT_LAUNCH(h, k_dref<3><<<grid, 128, 0, h->stream>>>(h->n_cells, h->n_el, h->n_nodes_cell, g, h->cell_nodes.p,
+                                                          h->mu_cell.p, h->lam, u_glob, T, h->minJ_cell.p));
+  LAT_CHECK_LAUNCH();
+  if (negJ) {
+    double* sc = scratch_scalars(h);
+    LAT_LAUNCH(h, k_min_reduce<<<1, 1024, 0, h->stream>>>((int)((int64_t)h->n_cells * nb), h->minJ_cell.p, sc));
     LAT_CHECK_LAUNCH();
     LAT_CUDA(cudaMemcpyAsync(h->h_pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));

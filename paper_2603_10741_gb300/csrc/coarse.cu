@@ -321,67 +321,78 @@ __global__ void k_cb_rhs(int64_t rows, const int* __restrict__ perm, const doubl
   rhs[t] = p >= 0 ? g[p] : 0.0;
 }
 
+// streaming 16-byte loads as volatile asm: issued in program order ahead of their uses, so that
+// a chunk's loads are all in flight before the first multiply-add
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+  float4 r;
+  asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p));
+  return r;
+}
+__device__ __forceinline__ double2 ld_stream2(const double2* p) {
+  double2 r;
+  asm volatile("ld.global.cs.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+  return r;
+}
+
 __global__ void __launch_bounds__(256) k_cb_step(int m, const double* __restrict__ M, const double* __restrict__ vin,
                                                  const double* __restrict__ rs, double* __restrict__ out) {
-  // m is even (padded blocks): a row is m / 2 16-byte pairs; every lane issues all its loads of a
-  // chunk (up to 12 in flight) before the first multiply-add
+  // m is even (padded blocks): a row is m / 2 16-byte pairs.  The block vector is staged in
+  // shared memory once per CTA; every lane then issues all its row loads of a chunk (up to 12
+  // in flight) before the first multiply-add, loads past the row end reading its last element
+  // (in bounds) weighted by 0
   constexpr int U = 12;
+  extern __shared__ __align__(16) double vsh[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) vsh[i] = vin[i];
+  __syncthreads();
   const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   const double2* a = reinterpret_cast<const double2*>(M + (size_t)row * m);
-  const double2* v = reinterpret_cast<const double2*>(vin);
+  const double2* v = reinterpret_cast<const double2*>(vsh);
   const int h2 = m >> 1;
   double acc0 = 0.0, acc1 = 0.0;
   for (int k0 = 0; k0 < h2; k0 += 32 * U) {
     double2 p[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + lane + 32 * u;
-      p[u] = k < h2 ? __ldcs(a + k) : make_double2(0.0, 0.0);
-    }
+    for (int u = 0; u < U; ++u) p[u] = ld_stream2(a + min(k0 + lane + 32 * u, h2 - 1));
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = k0 + lane + 32 * u;
-      if (k < h2) {
-        const double2 x = __ldg(v + k);
-        acc0 = fma(p[u].x, x.x, acc0);
-        acc1 = fma(p[u].y, x.y, acc1);
-      }
+      const double w = k < h2 ? 1.0 : 0.0;
+      const double2 x = v[min(k, h2 - 1)];
+      acc0 = fma(w * p[u].x, x.x, acc0);
+      acc1 = fma(w * p[u].y, x.y, acc1);
     }
   }
   const double s = warp_sum(acc0 + acc1);
   if (lane == 0) out[row] = rs[row] - s;
 }
 
-// the same with FP32 factors (mixed modes): products in FP32, vectors FP64; m a multiple of 4.
-// Every lane issues all its row loads before the first multiply-add (up to 12 16-byte loads in
-// flight per lane), so that a step's few hundred warps keep enough bytes in flight to stream the
-// block at HBM speed; longer rows loop.
+// the same with FP32 factors (mixed modes): products in FP32, vectors FP64 (staged as FP32 in
+// shared memory); m a multiple of 4
 __global__ void __launch_bounds__(256) k_cb_step32(int m, const float* __restrict__ M, const double* __restrict__ vin,
                                                    const double* __restrict__ rs, double* __restrict__ out) {
   constexpr int U = 12;
+  extern __shared__ __align__(16) float vshf[];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) vshf[i] = (float)vin[i];
+  __syncthreads();
   const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= m) return;
   const float4* a = reinterpret_cast<const float4*>(M + (size_t)row * m);
-  const double2* v = reinterpret_cast<const double2*>(vin);
+  const float4* v = reinterpret_cast<const float4*>(vshf);
   const int h4 = m >> 2;
   float acc = 0.f;
   for (int k0 = 0; k0 < h4; k0 += 32 * U) {
     float4 p[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + lane + 32 * u;
-      p[u] = k < h4 ? __ldcs(a + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    for (int u = 0; u < U; ++u) p[u] = ld_stream4(a + min(k0 + lane + 32 * u, h4 - 1));
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int k = k0 + lane + 32 * u;
-      if (k < h4) {
-        const double2 x0 = __ldg(v + 2 * k), x1 = __ldg(v + 2 * k + 1);
-        acc = fmaf(p[u].x, (float)x0.x, fmaf(p[u].y, (float)x0.y, fmaf(p[u].z, (float)x1.x, fmaf(p[u].w, (float)x1.y, acc))));
-      }
+      const float w = k < h4 ? 1.f : 0.f;
+      const float4 x = v[min(k, h4 - 1)];
+      acc = fmaf(w, fmaf(p[u].x, x.x, fmaf(p[u].y, x.y, fmaf(p[u].z, x.z, p[u].w * x.w))), acc);
     }
   }
 #pragma unroll
@@ -608,8 +619,8 @@ void run_coarse_block_solve(lat_ctx* h, const double* g, double* x) {
     const int rb_grid = (int)div_up(rows, 256), st_grid = (int)div_up((int64_t)m * 32, 256);
     const bool f32 = h->cb_U32.p != nullptr;
     auto step = [&](const double* M64, const float* M32, const double* vin, const double* rs, double* out) {
-      if (f32) LAT_LAUNCH(h, k_cb_step32<<<st_grid, 256, 0, h->stream>>>(m, M32, vin, rs, out));
-      else LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, 0, h->stream>>>(m, M64, vin, rs, out));
+      if (f32) LAT_LAUNCH(h, k_cb_step32<<<st_grid, 256, m * sizeof(float), h->stream>>>(m, M32, vin, rs, out));
+      else LAT_LAUNCH(h, k_cb_step<<<st_grid, 256, m * sizeof(double), h->stream>>>(m, M64, vin, rs, out));
     };
     LAT_LAUNCH(h, k_cb_rhs<<<rb_grid, 256, 0, h->stream>>>(rows, h->cb_perm.p, g, rb));
     LAT_CUDA(cudaMemcpyAsync(y, rb, m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));

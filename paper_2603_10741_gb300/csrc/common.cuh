@@ -146,6 +146,7 @@ struct lat_ctx {
   // selection state
   int n_r = 0;
   bool force_all = false;
+  int snap_kind = 0;                  // snapshots: 0 reduced-rule tangent data, 1 D^ref at the reduced points
   DBuf<int> S;                        // [n_r]
   DBuf<double> alpha;                 // [n_r][n_cells]
   DBuf<float> alpha32;
@@ -367,6 +368,7 @@ void run_residual(lat_ctx* h, const double* u_glob, double* f_cells, double* r_g
                   double* min_detF_host, bool* negJ);
 void run_tangent(lat_ctx* h, const double* u_glob, int quad, const int* cells, int n_sel,
                  double* K_out, bool* negJ, bool geometric = true);
+void run_dref_snapshots(lat_ctx* h, const double* u_glob, double* T, bool* negJ);
 void run_tangent_apply_exact(lat_ctx* h, const double* u_glob, const double* v_glob,
                              double* y_glob);
 void run_grad_mu(lat_ctx* h, const double* u_glob, const double* w_glob, double* grad);

@@ -1769,6 +1769,7 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->min_enrich >= 0 && o->min_enrich <= o->max_enrich, LAT_EINVAL, "min_enrich in [0, max_enrich]");
   LAT_REQUIRE(o->inner_its >= 0 && o->inner_its <= 190, LAT_EINVAL, "inner_its in [0, 190]");
   LAT_REQUIRE(o->inner_rtol >= 0 && o->inner_rtol < 1, LAT_EINVAL, "inner_rtol in [0, 1)");
+  LAT_REQUIRE(o->snapshot == 0 || o->snapshot == 1, LAT_EINVAL, "snapshot is 0 or 1");
 }
 
 // FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
@@ -1803,6 +1804,7 @@ extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
   o->min_enrich = 0;
   o->inner_its = h->prec == LAT_FP64 ? 0 : 20;
   o->inner_rtol = 1e-2;
+  o->snapshot = 0;
   return LAT_OK;
 }
 
@@ -1833,6 +1835,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     int it = 0;
     while (!(rn <= o->newton_rtol * r0 || rn <= floor) && it < cap) {
       double ta = now_ms();
+      h->snap_kind = o->snapshot;
       select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
       double tb = now_ms();
       R.t_select_ms += tb - ta;
@@ -1975,6 +1978,7 @@ extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_
     const double bnorm = run_norm_free(h, bF.p);
     LAT_CUDA(cudaMemsetAsync(lam.p, 0, nd * sizeof(double), h->stream));
     LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    h->snap_kind = o->snapshot;
     select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
     prepare_enriched(h, o, u);
     R.n_r_last = h->n_r;

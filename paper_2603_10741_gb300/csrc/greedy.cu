@@ -259,10 +259,19 @@ void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool
     LAT_LAUNCH(h, k_iota<<<div_up(h->n_cells, 256), 256, 0, h->stream>>>(h->n_cells, h->S.p));
     LAT_CHECK_LAUNCH();
   } else {
-    h->T.ensure((size_t)h->n_cells * h->nnz);
-    run_tangent(h, u_glob, 1, nullptr, h->n_cells, h->T.p, &neg);
+    // snapshots (Eq. snapshots): the reduced-rule local tangents' data, or the pulled-back
+    // tangent tensor at the reduced points (the Remark after it), one column per cell
+    int64_t rows = h->nnz;
+    if (h->snap_kind == 1) {
+      rows = (int64_t)h->n_el * h->dim * h->dim * h->dim * h->dim;
+      h->T.ensure((size_t)h->n_cells * rows);
+      run_dref_snapshots(h, u_glob, h->T.p, &neg);
+    } else {
+      h->T.ensure((size_t)h->n_cells * h->nnz);
+      run_tangent(h, u_glob, 1, nullptr, h->n_cells, h->T.p, &neg);
+    }
     LAT_REQUIRE(!neg, LAT_ENEG_JACOBIAN, "det F <= 0 in the snapshot evaluation");
-    run_greedy(h, h->T.p, h->nnz, h->n_cells, eps, max_nr, nullptr, nullptr, nullptr, nullptr,
+    run_greedy(h, h->T.p, rows, h->n_cells, eps, max_nr, nullptr, nullptr, nullptr, nullptr,
                nullptr, nullptr);
     LAT_REQUIRE(h->n_r > 0, LAT_EINVAL, "greedy selected no principal cell");
   }
@@ -276,6 +285,12 @@ void select_cells(lat_ctx* h, const double* u_glob, double eps, int max_nr, bool
     LAT_CHECK_LAUNCH();
   }
   ++h->sel_version;
+}
+
+extern "C" lat_status lattice_set_snapshots(lat_handle h, int32_t kind) {
+  if (!h || (kind != 0 && kind != 1)) return LAT_EINVAL;
+  h->snap_kind = kind;
+  return LAT_OK;
 }
 
 extern "C" lat_status select_principal_cells(lat_handle h, const double* u_glob, double eps,

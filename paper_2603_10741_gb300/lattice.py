@@ -21,6 +21,7 @@ STATUS = {0: "LAT_OK", 1: "LAT_EINVAL", 2: "LAT_ENOMEM", 3: "LAT_ECUDA", 4: "LAT
 EXPORTS = ["lattice_setup", "lattice_destroy", "lattice_sizes", "lattice_last_error",
            "lattice_set_mu_scale", "lattice_predictor", "lattice_gather", "assemble_residual_tangent",
            "greedy_select", "select_principal_cells", "set_principal_cells", "apply_reduced_tangent",
+           "lattice_set_snapshots",
            "lattice_default_opts",
            "newton_step", "adjoint_gradient", "feti_apply", "lattice_prepare_solver", "feti_to_global",
            "feti_from_global", "lattice_checkpoint_save", "lattice_checkpoint_load", "tangent_solve",
@@ -57,7 +58,8 @@ class NewtonOpts(C.Structure):
                 ("krylov_max_it", C.c_int32), ("krylov_restart", C.c_int32), ("pcg_iters", C.c_int32),
                 ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32),
                 ("max_enrich", C.c_int32), ("coarse_block_lu", C.c_int32), ("precond_tangent", C.c_int32),
-                ("min_enrich", C.c_int32), ("inner_its", C.c_int32), ("inner_rtol", C.c_double)]
+                ("min_enrich", C.c_int32), ("inner_its", C.c_int32), ("inner_rtol", C.c_double),
+                ("snapshot", C.c_int32)]
 
 
 class NewtonReport(C.Structure):
@@ -86,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "assemble_residual_tangent": [P, P, I32, P, I32, P, P, P, P],
         "greedy_select": [P, P, I64, I32, D, I32, P, P, P, P, P, P],
         "select_principal_cells": [P, P, D, I32, I32, P, P, P, P],
+        "lattice_set_snapshots": [P, I32],
         "set_principal_cells": [P, P, P, I32, P],
         "apply_reduced_tangent": [P, P, P, I32],
         "lattice_default_opts": [P, C.POINTER(NewtonOpts)],
@@ -248,6 +251,10 @@ class Lattice:
         return self.zeros(self.sizes.n_krylov)
 
     # --- entry points --------------------------------------------------------------------------
+    def lattice_set_snapshots(self, kind):
+        """Snapshot kind of select_principal_cells: 0 reduced-rule tangent data, 1 D^ref."""
+        self._check(self._lib.lattice_set_snapshots(self.h, int(kind)))
+
     def lattice_set_mu_scale(self, theta):
         th = np.ascontiguousarray(theta, dtype=np.float64)
         self._check(self._lib.lattice_set_mu_scale(self.h, th.ctypes.data))

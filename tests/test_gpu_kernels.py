@@ -346,3 +346,40 @@ def test_apply_node_groups(L, dims, n_r):
         Y = lat.apply_reduced_tangent(torch.tensor(X, device="cuda", dtype=dt)).cpu().numpy()
         assert _rel(Y[:, cells], Y_ref) < tol
         lat.close()
+
+
+@pytest.mark.parametrize("name,eps", [("ring4", 1e-3), ("strut2", 1e-3), ("strut222", 5e-3)])
+def test_dref_snapshot_selection_matches_oracle(L, name, eps):
+    """Principal cells from D^ref snapshots (the pulled-back tangent tensor at the one-point
+    rule, the Remark after Eq. snapshots): the same principal set, in the same order, and the same
+    coefficients as the oracle's Algorithm 1 on its own D^ref snapshots of every cell."""
+    case = latgen.make_case(name)
+    prob = Problem(case)
+    u = _state(case, 0.01, 23)
+    ul = prob.local(u)
+    T = OC.dref_snapshots(prob.cell, ul, prob.mu_cells, prob.lam)
+    g = OG.greedy(T, eps, 256)
+    al_ref = OG.alpha_triangular(T, g)
+    lat = L.Lattice.from_case(case)
+    lat.lattice_set_snapshots(1)
+    sel = lat.select_principal_cells(torch.tensor(u, device="cuda"), eps, 256)
+    assert sel["S"].cpu().numpy().tolist() == g.S.tolist()
+    al = sel["alpha"].cpu().numpy()
+    assert np.abs(al - al_ref).max() <= 1e-9 * max(1.0, np.abs(al_ref).max())
+    lat.close()
+
+
+def test_newton_with_dref_snapshots_ring4(L):
+    """Three load steps of the 4x4 ring lattice with principal cells chosen on D^ref snapshots
+    (FP64): the converged states are the oracle's (the snapshot kind changes the quasi-Newton
+    operator, not the solution)."""
+    from paper_2603_10741_gb300 import solve_load_path
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, _ = ON.load_path(prob, n_steps=3, tol=1e-12)
+    lat = L.Lattice.from_case(case)
+    opts = lat.lattice_default_opts(newton_rtol=1e-12, snapshot=1)
+    u, reps = solve_load_path(lat, case, opts, steps=3)
+    err = np.linalg.norm(u.cpu().numpy() - ref[-1]) / np.linalg.norm(ref[-1])
+    assert err < 1e-10, err
+    lat.close()
