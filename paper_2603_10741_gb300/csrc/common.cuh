@@ -423,6 +423,7 @@ bool coarse_block_plan(lat_ctx* h);
 constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
 constexpr int kWideSweepRows = 512;           // block-LU steps of larger blocks run over the whole GPU
 constexpr int kTcCells = 128;                 // cells per tensor-core tile (the MMA's N)
+constexpr int kTcRowTiles = 1;                // 128-row tiles per tensor-core CTA (sharing each B panel)
 void run_coarse_block_solve(lat_ctx* h, const double* g, double* x);
 void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)

@@ -43,7 +43,7 @@ struct TcCfg {
   // a stage holds one K panel of both BF16 halves of A (MW tiles) and of B: the three products
   // of the panel are issued from one load
   static constexpr int STAGE_BYTES = 2 * (MW * A_BYTES + B_BYTES);
-  static constexpr int STAGES = 3;   // TN = 128: 3 x 64 KiB
+  static constexpr int STAGES = MW == 1 ? 3 : 2;   // TN = 128: 3 x 64 KiB, or 2 x 96 KiB for two M tiles
   static constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES;
   static constexpr int TMEM_COLS = MW * TN;   // MW accumulators of TN FP32 columns
   // instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, N >> 3, M >> 4
@@ -430,7 +430,7 @@ void launch_sdd_tc(lat_ctx* h, const double* X, double* Y) {
 // Y (rows of every cell, per the view: see KinvMode) = [G; Phi^T] X on the tensor cores, on
 // 128-cell tiles of each key's cells, one CTA per SM.
 void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
-  launch_tc<kTcCells, 1>(h, X, Y, mode, h->tile_seg_tc.p, h->tile_c0_tc.p, h->max_tiles_tc);
+  launch_tc<kTcCells, kTcRowTiles>(h, X, Y, mode, h->tile_seg_tc.p, h->tile_c0_tc.p, h->max_tiles_tc);
 }
 
 void run_sdd_tc(lat_ctx* h, const double* X, double* Y) { launch_sdd_tc<kTcCells>(h, X, Y); }
