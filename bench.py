@@ -323,7 +323,7 @@ def roofline_entry(name, k, s, n_r, precision, hbm_peak, bf16_peak, peak_src):
                 "frac": ach / hbm_peak, "peak_source": "%s copy bandwidth" % peak_src, "work_per_launch": work,
                 "avg_us": k["avg_us"], "launches": k["launches"], "share": k.get("share")}
     if kind == "tensor":
-        peak, src = bf16_peak, "%s bf16 tensor (burst)" % peak_src
+        peak, src = bf16_peak, "%s bf16 tensor (sustained)" % peak_src
     elif kind == "fp64" or precision == "fp64":
         peak, src = FP64_PEAK_TFLOPS, "FP64 ALU, recipe table (1.20 measured with an FMA loop)"
     else:
@@ -354,7 +354,8 @@ def run_ours(args):
 
     ws, rank, local = dist_init(args)
     dev = torch.device("cuda", torch.cuda.current_device())
-    hbm_peak, bf16_peak, _, peak_src = peaks()
+    # the tensor-core product runs inside a seconds-long step: the sustained BF16 peak
+    hbm_peak, _, bf16_peak, peak_src = peaks()
     prec = {"fp64": LAT_FP64, "fp32": LAT_MIXED_FP32, "bf16": LAT_MIXED_BF16}[args.precision]
     case = latgen.make_case(args.case)
     stream = torch.cuda.current_stream()
@@ -437,7 +438,10 @@ def run_ours(args):
     detail["kernels"] = kt
     detail["kernel_rooflines"] = rl
     detail["timed_iteration_reports"] = reps
-    roof = dict(rl[0]) if rl else None
+    # the dominant kernel: the timers that bracket one launch each, with the four views of the
+    # tensor-core product (one kernel, k_local_tc) taken together; the coarse solve (a chain of
+    # launches whose host-side issue the per-launch timers stretch) is reported in the detail
+    roof = dominant_kernel(rl)
     if roof:
         tr = MEASURED_TRAFFIC.get((args.case, args.precision, roof["kernel"]))
         roof["traffic"] = tr[0] if tr else None
@@ -496,6 +500,35 @@ def run_ours(args):
                 json.dump(detail, f, indent=1, default=str)
         print(json.dumps(compact(out)))
     return 0
+
+
+TC_VIEWS = ("local_tc", "local_tc_dual", "local_tc_dual_in", "dual_schur_tc")
+SINGLE_LAUNCH = TC_VIEWS + ("apply_reduced", "apply_reduced_fp32", "apply_percell", "apply_percell_fp32",
+                            "residual", "local_segmm", "local_segmm_dual", "local_segmm_dual_in", "local_gemv",
+                            "local_gemv_dual", "local_gemv_dual_in", "dual_schur", "gj_update", "coarse_gemv")
+
+
+def dominant_kernel(rl):
+    """Roofline entry of the kernel with the largest total time (tensor-core views combined)."""
+    tc = [e for e in rl if e["kernel"] in TC_VIEWS]
+    cand = [dict(e) for e in rl if e["kernel"] in SINGLE_LAUNCH and e["kernel"] not in TC_VIEWS]
+    if tc:
+        launches = sum(e["launches"] for e in tc)
+        total_us = sum(e["avg_us"] * e["launches"] for e in tc)
+        work = sum(e["work_per_launch"] * e["launches"] for e in tc) / launches
+        ach = work / (total_us / launches * 1e-6) / 1e12
+        cand.append({"kernel": "k_local_tc (" + ", ".join(e["kernel"] for e in tc) + ")", "bound": "tensor",
+                     "achieved": ach, "peak": tc[0]["peak"], "unit": "TFLOP/s", "frac": ach / tc[0]["peak"],
+                     "peak_source": tc[0]["peak_source"], "work_per_launch": work, "avg_us": total_us / launches,
+                     "launches": launches, "share": sum(e["share"] or 0 for e in tc),
+                     "issued_frac": 3 * ach / tc[0]["peak"]})
+    if not cand:
+        return None
+    for e in cand:
+        e["_total"] = e["avg_us"] * e["launches"]
+    best = max(cand, key=lambda e: e["_total"])
+    best.pop("_total", None)
+    return best
 
 
 def compact(out):

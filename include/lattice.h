@@ -221,7 +221,10 @@ typedef struct {
                               FP64 (two sequential sweeps over the cell layers, factors N m^3,
                               no explicit inverse; a sweep step is one thread-block cluster for
                               blocks up to 512 rows, one launch over the whole GPU for larger
-                              ones), 2 block LU with the whole-GPU steps at any block size, 0 the
+                              ones), 2 block LU with the whole-GPU steps at any block size, 3
+                              block LU with the cluster sweeps in the forms taken when larger
+                              blocks do not fit (8-CTA clusters, block rows read from global
+                              memory instead of prefetched), 0 the
                               explicit inverse (N^2 m^3 to build, one dense product per solve;
                               FP32 copy in the mixed modes), -1 (default) block LU when the
                               explicit inverse would hold more than 8192^2 entries (N blocks of

@@ -562,15 +562,16 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense) {
 
 // Cluster size and shared memory of the FP64 block-LU sweeps; false when the device runs no
 // cluster of at least 8 CTAs with them (the dense inverse is used then).
-bool coarse_block_plan(lat_ctx* h) {
+bool coarse_block_plan(lat_ctx* h, bool fallback) {
   const int m = h->cb_m;
   for (int C : {16, 8}) {
+    if (fallback && C == 16) continue;   // the forms taken when 16-CTA clusters or prefetch do not fit
     const int R = div_up(m, C);
     const int mp = (m + 1) & ~1, Rp = (R + 1) & ~1;
     const size_t base = (size_t)(2 * mp + 2 * (size_t)h->cb_n * Rp) * sizeof(double);
     size_t shm = base + 2 * (size_t)R * m * sizeof(double);
     int pre = 1;
-    if (shm > 200 * 1024) {
+    if (shm > 200 * 1024 || fallback) {
       shm = base;
       pre = 0;
     }

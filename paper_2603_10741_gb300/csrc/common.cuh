@@ -122,6 +122,8 @@ struct lat_ctx {
   DBuf<int> lam_p, lam_m;             // [n_lambda] local entries of the +/- copies
   DBuf<int> dual_entry, dual_l1, dual_l2;  // dual copies and their multipliers (+-(l+1), 0 = none)
   DBuf<double> dual_scale;            // [n_dual] 1/multiplicity of the node
+  DBuf<int2> dual_lk;                 // [n_D][n_cells] signed multipliers (l1, l2) of each dual copy
+  DBuf<float> dual_lsc;               // [n_D][n_cells] its 1/multiplicity
   int64_t n_dual = 0;
   int n_classes = 0;
   DBuf<int> cell_class;               // [n_cells] boundary-condition class
@@ -419,7 +421,7 @@ void prepare_enriched(lat_ctx* h, const lat_newton_opts* o, const double* u_glob
 void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit, int split = -1,
                double* snap = nullptr);
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
-bool coarse_block_plan(lat_ctx* h);
+bool coarse_block_plan(lat_ctx* h, bool fallback = false);
 constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
 constexpr int kWideSweepRows = 512;           // block-LU steps of larger blocks run over the whole GPU
 constexpr int kTcCells = 128;                 // cells per tensor-core tile (the MMA's N)
@@ -429,4 +431,5 @@ void run_g_to_bf16(lat_ctx* h, size_t n);
 // which part of the local inverse a product uses (see kinv in feti.cu)
 enum KinvMode { KINV_FULL = 0, KINV_DUAL = 1, KINV_DUAL_IN = 2 };
 void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode);
-void run_sdd_tc(lat_ctx* h, const double* X, double* Y);
+void run_sdd_tc(lat_ctx* h, const double* X, double* Y, const double* lam = nullptr);
+void run_local_tc_lam(lat_ctx* h, const double* lam, double* Y);

@@ -1157,10 +1157,10 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_gl
   // inverse is kept while it is small; its N^2 m^3 build and N^2 m^2 storage decide beyond that.
   const int64_t np = h->n_primal;
   const int want = o ? o->coarse_block_lu : -1;
-  h->cb_wide = want == 2 || h->cb_m > kWideSweepRows;
+  h->cb_wide = want == 2 || (want != 3 && h->cb_m > kWideSweepRows);
   h->cb_solve = np > 0 && h->coarse_blocked &&
                 (want >= 1 || (want < 0 && (int64_t)h->cb_n * h->cb_m > kDenseCoarseLimit)) &&
-                (h->cb_wide || coarse_block_plan(h));
+                (h->cb_wide || coarse_block_plan(h, want == 3));
   if (h->cb_solve) {
     h->CoarseInv.release();
     h->CoarseInv32.release();
@@ -1290,7 +1290,9 @@ void run_coarse_solve(lat_ctx* h, const double* g, double* x) {
 //   KINV_DUAL     the same, and only the dual and corner rows of w are formed (the interface
 //                 operator B K^-rom B^T reads no others): the trailing dual block,
 //                 (n_R - n_I + n_P) x (n_R - n_I) instead of (n_R + n_P) x n_R.
-void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
+//   lam (KINV_DUAL on the tensor-core path only): v is B^T lam on the dual DOFs and zero
+//                 elsewhere, formed by the product's operand packing (v is not read).
+void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL, const double* lam = nullptr) {
   const int ns = h->n_cells, nR = h->n_R, nP = h->n_P;
   const int lo_r = mode == KINV_DUAL ? h->n_I : 0;   // first row and column of the view
   const int lo_c = mode == KINV_FULL ? 0 : h->n_I;
@@ -1318,7 +1320,9 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
           h->key_slot.p, h->c_cell.p, rr, rc, h->pdofs.p, v, wl));
     }
   } else if (h->prec == LAT_MIXED_BF16) {
-    run_local_tc(h, v, wl, mode);   // tcgen05, BF16 operands, FP32 accumulation
+    // tcgen05, BF16 operands, FP32 accumulation
+    if (lam) run_local_tc_lam(h, lam, wl);
+    else run_local_tc(h, v, wl, mode);
   } else {
     KernelTimer kt(h, tg_segmm[mode]);
     dim3 grid(h->max_tiles, div_up(nKr + nP, 64));
@@ -1333,7 +1337,7 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
   if (h->n_primal) {
     // g_P = v_P + sum_s A_P^T Phi^T v_R   (from the corner rows of wl)
     LAT_LAUNCH(h, k_primal_assemble<<<div_up(h->n_primal, 256), 256, 0, h->stream>>>(h->n_primal, h->p_copy_ptr.p,
-        h->p_copy.p, wl, h->gP.p, 1, pr_of(h, v)));
+        h->p_copy.p, wl, h->gP.p, lam ? 0 : 1, lam ? nullptr : pr_of(h, v)));
     run_coarse_solve(h, h->gP.p, pr_of(h, w));
   }
   if (h->n_primal) {
@@ -1364,13 +1368,21 @@ void kinv(lat_ctx* h, const double* v, double* w, KinvMode mode = KINV_FULL) {
 }
 
 // S_op p = B K^-rom B^T p (multiplier vectors); uses tmp (saddle sized) as scratch
+// the tensor-core path forms B^T lambda inside its operand packing (no zeroed local vector, no
+// scatter): BF16 mode with the segmented products (few keys)
+bool fused_dual(const lat_ctx* h) { return h->prec == LAT_MIXED_BF16 && (int64_t)h->n_keys * 8 <= h->n_cells; }
+
 void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
-  LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
-  LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, nullptr, p, 1.0, t1));
-  LAT_CHECK_LAUNCH();
-  kinv(h, t1, t2, KINV_DUAL);   // t1 vanishes off the dual DOFs; only dual rows of t2 are read
+  if (fused_dual(h)) {
+    kinv(h, nullptr, t2, KINV_DUAL, p);
+  } else {
+    LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
+    LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                            h->dual_l2.p, nullptr, p, 1.0, t1));
+    LAT_CHECK_LAUNCH();
+    kinv(h, t1, t2, KINV_DUAL);   // t1 vanishes off the dual DOFs; only dual rows of t2 are read
+  }
   LAT_LAUNCH(h, k_jump<<<div_up(h->n_lambda, 256), 256, 0, h->stream>>>(h->n_lambda, h->lam_p.p, h->lam_m.p, t2, 1.0, q, 0));
   LAT_CHECK_LAUNCH();
 }
@@ -1378,18 +1390,21 @@ void dual_op(lat_ctx* h, const double* p, double* q, double* t1, double* t2) {
 // lumped preconditioner z = B_D K~_dd B_D^T r
 void dual_precond(lat_ctx* h, const double* r, double* z, double* t1, double* t2, double* wloc) {
   const int64_t nloc = (int64_t)h->n_loc * h->n_cells;
-  LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
-  LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
-                                                          h->dual_l2.p, h->dual_scale.p, r, 1.0, t1));
-  LAT_CHECK_LAUNCH();
+  const bool fused = h->iface == 0 && fused_dual(h);
+  if (!fused) {
+    LAT_CUDA(cudaMemsetAsync(t1, 0, (nloc + h->n_primal) * sizeof(double), h->stream));
+    LAT_LAUNCH(h, k_jump_t<<<div_up(h->n_dual, 256), 256, 0, h->stream>>>(h->n_dual, h->dual_entry.p, h->dual_l1.p,
+                                                            h->dual_l2.p, h->dual_scale.p, r, 1.0, t1));
+    LAT_CHECK_LAUNCH();
+  }
   if (h->iface == 0) {
     // Dirichlet: local dual Schur complements of the cells' principals, c_s S_DD^{slot(s)} x_D;
     // with few keys as a segmented product over the key-ordered cells (as the local inverses)
     const int nD = h->n_R - h->n_I;
     const size_t shm = (size_t)nD * sizeof(double);
     const bool seg = (int64_t)h->n_keys * 8 <= h->n_cells;
-    if (seg && h->prec == LAT_MIXED_BF16) {
-      run_sdd_tc(h, t1, t2);   // tcgen05, BF16 operand pairs, FP32 accumulation
+    if (fused) {
+      run_sdd_tc(h, nullptr, t2, r);   // tcgen05, BF16 operand pairs, FP32 accumulation; operand B_D^T r
     } else if (seg) {
       KernelTimer kt(h, "dual_schur");
       const int* rd = h->rdofs.p + h->n_I;
@@ -1764,7 +1779,7 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->pcg_rtol >= 0 && o->pcg_rtol < 1, LAT_EINVAL, "pcg_rtol in [0, 1)");
   LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
   LAT_REQUIRE(o->max_enrich >= 0 && o->max_enrich <= 6, LAT_EINVAL, "max_enrich in [0, 6]");
-  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 2, LAT_EINVAL, "coarse_block_lu in {-1, 0, 1, 2}");
+  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 3, LAT_EINVAL, "coarse_block_lu in [-1, 3]");
   LAT_REQUIRE(o->precond_tangent >= -1 && o->precond_tangent <= 1, LAT_EINVAL, "precond_tangent in {-1, 0, 1}");
   LAT_REQUIRE(o->min_enrich >= 0 && o->min_enrich <= o->max_enrich, LAT_EINVAL, "min_enrich in [0, max_enrich]");
   LAT_REQUIRE(o->inner_its >= 0 && o->inner_its <= 190, LAT_EINVAL, "inner_its in [0, 190]");

@@ -403,6 +403,22 @@ void build_feti_impl(lat_ctx* h, int level) {
     dsc.push_back(dscale[kv.first]);
   }
   h->n_dual = (int64_t)de.size();
+  // per (dual DOF position, cell) the signed multipliers of the copy and its scale: the
+  // interface products of the tensor-core path read B^T lambda from it directly
+  {
+    const int nI = h->n_I, nD = h->n_R - h->n_I;
+    std::vector<int2> lk((size_t)nD * ns, make_int2(0, 0));
+    std::vector<float> lsc((size_t)nD * ns, 0.f);
+    for (size_t q = 0; q < de.size(); ++q) {
+      const int e = de[q], kl = e / ns, sc = e % ns;
+      const int gk = rpos[kl] - nI;
+      if (gk < 0) continue;   // a dual entry is a remaining, non-interior DOF
+      lk[(size_t)gk * ns + sc] = make_int2(d1[q], d2[q]);
+      lsc[(size_t)gk * ns + sc] = (float)dsc[q];
+    }
+    h->dual_lk.upload(lk, h->stream);
+    h->dual_lsc.upload(lsc, h->stream);
+  }
   h->dual_entry.upload(de, h->stream);
   h->dual_l1.upload(d1, h->stream);
   h->dual_l2.upload(d2, h->stream);
@@ -605,7 +621,7 @@ extern "C" lat_status lattice_destroy(lat_handle h) {
   rel(h->copy_ptr); rel(h->copy_idx); rel(h->dof_fixed); rel(h->dir_unit); rel(h->aff_unit);
   rel(h->corner_of_node); rel(h->rdofs); rel(h->pdofs); rel(h->rpos); rel(h->pidx);
   rel(h->p_copy_ptr); rel(h->p_copy); rel(h->loc_fixed); rel(h->lam_p); rel(h->lam_m);
-  rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->cell_class);
+  rel(h->dual_entry); rel(h->dual_l1); rel(h->dual_l2); rel(h->dual_scale); rel(h->dual_lk); rel(h->dual_lsc); rel(h->cell_class);
   rel(h->coarse_ptr); rel(h->coarse_src); rel(h->cb_dest); rel(h->cb_perm); rel(h->cb_A);
   rel(h->cb_Dinv); rel(h->cb_Einv); rel(h->cb_U); rel(h->cb_V); rel(h->cb_T); rel(h->cb_X); rel(h->cb_Ut); rel(h->cb_y); rel(h->cb_w); rel(h->coarse_row); rel(h->coarse_col);
   rel(h->S); rel(h->alpha); rel(h->alpha32); rel(h->Kp); rel(h->Kp32); rel(h->Kg);

@@ -316,6 +316,45 @@ __global__ void k_pack_xt(int n_cells, int n_K, int KP, const double* __restrict
   }
 }
 
+// the same tiles for an operand supported on the dual DOFs and given as B^T lambda (scaled by
+// 1/multiplicity when lsc is given): each copy's value is formed from its multipliers through
+// the per-(dual DOF, cell) table instead of being scattered into a zeroed local vector first
+template <int TN>
+__global__ void k_pack_lam(int n_cells, int n_D, int KP, const double* __restrict__ lam, const int2* __restrict__ lk,
+                           const float* __restrict__ lsc, const int* __restrict__ tile_seg,
+                           const int* __restrict__ tile_c0, const int* __restrict__ seg_ptr,
+                           const int* __restrict__ perm, __nv_bfloat16* __restrict__ XT) {
+  constexpr int BE = TN * TK;
+  __shared__ __align__(16) __nv_bfloat16 hi[BE], lo[BE];
+  const int tile = blockIdx.x, kp = blockIdx.y;
+  const int c0 = tile_c0[tile];
+  const int c_end = seg_ptr[tile_seg[tile] + 1];
+  for (int t = threadIdx.x; t < TN * TK; t += blockDim.x) {
+    const int k = t / TN, c = t % TN;                          // consecutive threads: consecutive cells
+    const int pos = c0 + c, gk = kp * TK + k;
+    float v = 0.f;
+    if (pos < c_end && gk < n_D) {
+      const size_t q = (size_t)gk * n_cells + perm[pos];
+      const int2 l = lk[q];
+      double a = 0.0;
+      if (l.x) a += (l.x > 0 ? 1.0 : -1.0) * lam[abs(l.x) - 1];
+      if (l.y) a += (l.y > 0 ? 1.0 : -1.0) * lam[abs(l.y) - 1];
+      if (lsc) a *= (double)lsc[q];
+      v = (float)a;
+    }
+    const __nv_bfloat16 h = __float2bfloat16(v);
+    hi[core_off(c, k)] = h;
+    lo[core_off(c, k)] = __float2bfloat16(v - __bfloat162float(h));
+  }
+  __syncthreads();
+  uint4* dh = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + kp) * BE);
+  uint4* dl = reinterpret_cast<uint4*>(XT + ((size_t)tile * 2 * KP + KP + kp) * BE);
+  for (int t = threadIdx.x; t < BE / 8; t += blockDim.x) {
+    dh[t] = reinterpret_cast<const uint4*>(hi)[t];
+    dl[t] = reinterpret_cast<const uint4*>(lo)[t];
+  }
+}
+
 // a view of G (rows_v rows of n_K columns from (G, row stride ldsrc, key stride kstride)) as BF16
 // pairs in the tiled layout: GT[key][mt][kp][core_off(r, k)] high parts, the low parts
 // (BF16 rounding of G - hi) lo_off elements later; zero outside the view
@@ -378,7 +417,8 @@ void run_g_to_bf16(lat_ctx* h, size_t n) {
 namespace {
 
 template <int TN, int MW>
-void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int* tseg, const int* tc0, int n_tiles) {
+void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int* tseg, const int* tc0, int n_tiles,
+               const double* lam = nullptr) {
   using C = TcCfg<TN, MW>;
   const int lo_r = mode == KINV_DUAL ? h->n_I : 0, lo_c = mode == KINV_FULL ? 0 : h->n_I;
   const int nKr = h->n_R - lo_r, nKc = h->n_R - lo_c;
@@ -388,8 +428,13 @@ void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int*
   const int* rc = h->rdofs.p + lo_c;
   const int KPmax = std::max(1, div_up(h->n_R, TK));
   h->Xb16.ensure((size_t)n_tiles * 2 * KPmax * C::B_ELEMS);
-  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(n_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nKc, KP, X, tseg, tc0,
-                                                                         h->seg_ptr.p, h->perm.p, rc, h->Xb16.p));
+  if (lam)   // the dual view's operand is B^T lambda (mode KINV_DUAL: columns = the dual DOFs)
+    LAT_LAUNCH(h, k_pack_lam<TN><<<dim3(n_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nKc, KP, lam, h->dual_lk.p,
+                                                                            nullptr, tseg, tc0, h->seg_ptr.p,
+                                                                            h->perm.p, h->Xb16.p));
+  else
+    LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(n_tiles, KP), 256, 0, h->stream>>>(h->n_cells, nKc, KP, X, tseg, tc0,
+                                                                           h->seg_ptr.p, h->perm.p, rc, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc<TN, MW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM_BYTES));
   dim3 grid(n_tiles, div_up(MT, MW));
@@ -404,7 +449,7 @@ void launch_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode, const int*
 // the Dirichlet interface preconditioner's local products y_D = c_s S_DD x_D on the same tiles
 // (dual rows and columns, no corner rows, scaled by c_s)
 template <int TN>
-void launch_sdd_tc(lat_ctx* h, const double* X, double* Y) {
+void launch_sdd_tc(lat_ctx* h, const double* X, double* Y, const double* lam) {
   using C = TcCfg<TN, 1>;
   const int nD = h->n_R - h->n_I;
   const int MT = div_up(nD, TM);
@@ -412,9 +457,14 @@ void launch_sdd_tc(lat_ctx* h, const double* X, double* Y) {
   const int* rd = h->rdofs.p + h->n_I;
   const int KPmax = std::max(1, div_up(h->n_R, TK));
   h->Xb16.ensure((size_t)h->max_tiles_tc * 2 * KPmax * C::B_ELEMS);
-  LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(h->max_tiles_tc, KP), 256, 0, h->stream>>>(h->n_cells, nD, KP, X, h->tile_seg_tc.p,
-                                                                              h->tile_c0_tc.p, h->seg_ptr.p, h->perm.p,
-                                                                              rd, h->Xb16.p));
+  if (lam)   // the operand is B_D^T lambda: B^T lambda scaled by 1/multiplicity
+    LAT_LAUNCH(h, k_pack_lam<TN><<<dim3(h->max_tiles_tc, KP), 256, 0, h->stream>>>(
+                      h->n_cells, nD, KP, lam, h->dual_lk.p, h->dual_lsc.p, h->tile_seg_tc.p, h->tile_c0_tc.p,
+                      h->seg_ptr.p, h->perm.p, h->Xb16.p));
+  else
+    LAT_LAUNCH(h, k_pack_xt<TN><<<dim3(h->max_tiles_tc, KP), 256, 0, h->stream>>>(h->n_cells, nD, KP, X, h->tile_seg_tc.p,
+                                                                                h->tile_c0_tc.p, h->seg_ptr.p, h->perm.p,
+                                                                                rd, h->Xb16.p));
   LAT_CUDA(cudaFuncSetAttribute(k_local_tc<TN, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)C::SMEM_BYTES));
   dim3 grid(h->max_tiles_tc, MT);
@@ -433,4 +483,9 @@ void run_local_tc(lat_ctx* h, const double* X, double* Y, KinvMode mode) {
   launch_tc<kTcCells, kTcRowTiles>(h, X, Y, mode, h->tile_seg_tc.p, h->tile_c0_tc.p, h->max_tiles_tc);
 }
 
-void run_sdd_tc(lat_ctx* h, const double* X, double* Y) { launch_sdd_tc<kTcCells>(h, X, Y); }
+void run_sdd_tc(lat_ctx* h, const double* X, double* Y, const double* lam) { launch_sdd_tc<kTcCells>(h, X, Y, lam); }
+
+// the dual view of [G; Phi^T] applied to B^T lambda (the interface operator's local products)
+void run_local_tc_lam(lat_ctx* h, const double* lam, double* Y) {
+  launch_tc<kTcCells, kTcRowTiles>(h, nullptr, Y, KINV_DUAL, h->tile_seg_tc.p, h->tile_c0_tc.p, h->max_tiles_tc, lam);
+}

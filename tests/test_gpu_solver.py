@@ -235,7 +235,8 @@ def test_newton_bf16_mode_ring4(L):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_blocked_coarse_inverse_matches_dense(L, precision):
     """Coarse solves on the 8x8 ring lattice: the block-LU sweeps over the cell layers (one
-    cluster per sweep, and one whole-GPU launch per step) and the block-tridiagonal explicit
+    16-CTA cluster per sweep with prefetched rows; one 8-CTA cluster reading rows from global
+    memory; one whole-GPU launch per step) and the block-tridiagonal explicit
     inverse equal the dense inverse of the unlayered coarse matrix, and
     with every cell principal K^-rom stays the exact inverse of K~ in FP64.  In the FP32 mode
     (FP32 local inverses; the block-LU solve stays FP64, the explicit inverse is applied as an FP32
@@ -246,7 +247,7 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
     arrays = L.case_arrays(case)
     outs = []
     tol = 1e-9 if precision == 0 else 1e-5
-    for layered, block_lu in ((True, 1), (True, 2), (True, 0), (False, 0)):
+    for layered, block_lu in ((True, 1), (True, 2), (True, 3), (True, 0), (False, 0)):
         a = dict(arrays)
         if not layered:
             a["cell_layer"] = None
@@ -269,10 +270,10 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
             assert err < 1e-9, (layered, block_lu, err)
         outs.append(back[:nd].cpu().numpy())
         lat.close()
-    ref = np.abs(outs[3]).max()
-    assert np.abs(outs[0] - outs[3]).max() < tol * ref
-    assert np.abs(outs[1] - outs[3]).max() < tol * ref
-    assert np.abs(outs[2] - outs[3]).max() < (1e-10 if precision == 0 else tol) * ref
+    ref = np.abs(outs[4]).max()
+    for k in range(3):
+        assert np.abs(outs[k] - outs[4]).max() < tol * ref, k
+    assert np.abs(outs[3] - outs[4]).max() < (1e-10 if precision == 0 else tol) * ref
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
