@@ -220,8 +220,11 @@ typedef struct {
   int32_t coarse_block_lu; /* coarse solves of a block-tridiagonal coarse matrix: 1 block LU in
                               FP64 (two sequential sweeps over the cell layers, factors N m^3,
                               no explicit inverse; a sweep step is one thread-block cluster for
-                              blocks up to 512 rows, one launch over the whole GPU for larger
-                              ones), 2 block LU with the whole-GPU steps at any block size, 3
+                              blocks up to 512 rows, for larger ones the whole solve as one
+                              cooperative launch over the whole GPU with a grid-wide barrier
+                              between steps), 2 block LU with one whole-GPU launch per step at
+                              any block size, 4 block LU as the single cooperative launch at any
+                              block size, 3
                               block LU with the cluster sweeps in the forms taken when larger
                               blocks do not fit (8-CTA clusters, block rows read from global
                               memory instead of prefetched), 0 the
@@ -250,6 +253,16 @@ typedef struct {
                               tangent tensor D^ref (Eq. tensorfunctionPulledback) at the
                               one-point rule of every element (the Remark after Eq. snapshots:
                               n_el d^4 values per cell instead of nnz) */
+  int32_t eps_refine;      /* greedy tolerance tightenings per call (newton_step and
+                              adjoint_gradient), each dividing eps by 10 and kept for the rest of
+                              the call: when the line search finds no acceptable step along the
+                              reduced-tangent direction (the iteration is then repeated from the
+                              same iterate), when two accepted Newton steps in a row each reduce
+                              ||r_F|| by less than the factor eps_refine_rate, and when an
+                              adjoint defect correction does (the reduced tangent then limits
+                              the linear convergence).  0: eps is fixed and a rejected direction
+                              ends the call with an error */
+  double eps_refine_rate;  /* contraction factor of that test (default 0.5) */
 } lat_newton_opts;
 
 typedef struct {
@@ -264,6 +277,8 @@ typedef struct {
   int32_t pcg_its_total;   /* interface PCG iterations inside the preconditioner */
   int32_t enrich_level;    /* primal enrichment level in use at exit */
   int32_t inner_its_total; /* inner FP32-operator GMRES iterations (mixed modes, inner_its > 0) */
+  int32_t eps_refinements; /* greedy tolerance tightenings of this call (eps_refine) */
+  double eps_last;         /* greedy tolerance in use at exit */
 } lat_newton_report;
 
 /* Default options (eps 3e-4 in 2D and 5e-3 in 3D, max_nr 256, newton_rtol 1e-8, krylov_rtol
@@ -271,7 +286,8 @@ typedef struct {
  * iterations, Armijo cap 30, Dirichlet interface preconditioner, enrichment up to level 3,
  * preconditioner from the full tangent in 2D and from its material part in 3D, starting
  * enrichment level 0; in the mixed modes an inner FP32-operator GMRES of at most 20 iterations
- * to 1e-2 as FGMRES's preconditioner). */
+ * to 1e-2 as FGMRES's preconditioner; up to 2 tenfold tolerance tightenings per call, on
+ * rejected directions or a contraction above 0.5). */
 lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 
 /* Newton-Raphson for one load step (Section 2.2.5) from the initial guess in u_glob (dev,

@@ -421,6 +421,202 @@ __global__ void k_d2f_blocks(int64_t n, const double* __restrict__ x, float* __r
     y[i] = (float)x[i];
 }
 
+// The whole block-LU solve in one cooperative launch (one CTA per SM, every CTA resident): the
+// right-hand side gather, the forward recurrence y_b = g_b - U_{b-1}^T y_{b-1}, w = D^{-1} y,
+// the backward recurrence x_b = w_b - U_b x_{b+1} and the scatter, with a grid-wide barrier
+// between dependent steps instead of a kernel launch.  CTA c owns rows [c m / G, (c + 1) m / G)
+// of every step's m x m block; those rows are contiguous, and one bulk copy (cp.async.bulk,
+// completing on an mbarrier) brings the rows of step k + 2 into a shared-memory buffer while
+// steps k and k + 1 run, so a step waits only for its input vector (staged in shared memory by
+// every CTA), a product from shared memory and the barrier.  w = D^{-1} y streams its N blocks
+// from global memory with a warp per row over the whole GPU.  T = float for the FP32 factor
+// copies of the mixed modes (FP32 products, as the per-step kernels), double otherwise; m is a
+// multiple of 4 (16-byte rows).  A bulk copy that has not landed after a bounded wait sets bit 8
+// of *err; the kernel still passes every grid barrier and waits once more for such a copy
+// before it returns.
+constexpr int kCoopThreads = 512;
+
+template <typename T> struct CoopVec;
+template <> struct CoopVec<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static float dot(const float4& a, const float4& b, float acc) {
+    acc = fmaf(a.x, b.x, acc);
+    acc = fmaf(a.y, b.y, acc);
+    acc = fmaf(a.z, b.z, acc);
+    return fmaf(a.w, b.w, acc);
+  }
+  __device__ static float4 from(const double* v) {
+    const double2 p = __ldcg(reinterpret_cast<const double2*>(v));
+    const double2 q = __ldcg(reinterpret_cast<const double2*>(v) + 1);
+    return make_float4((float)p.x, (float)p.y, (float)q.x, (float)q.y);
+  }
+};
+template <> struct CoopVec<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static double dot(const double2& a, const double2& b, double acc) {
+    acc = fma(a.x, b.x, acc);
+    return fma(a.y, b.y, acc);
+  }
+  __device__ static double2 from(const double* v) { return __ldcg(reinterpret_cast<const double2*>(v)); }
+};
+
+// one row of a block (shared or global memory) against a vector staged in shared memory
+template <typename T>
+__device__ __forceinline__ T coop_row_dot(const T* a, const T* v, int m, int lane) {
+  using CV = CoopVec<T>;
+  using V = typename CV::V;
+  const V* a4 = reinterpret_cast<const V*>(a);
+  const V* v4 = reinterpret_cast<const V*>(v);
+  const int n4 = m / CV::W;
+  T acc0 = 0, acc1 = 0;
+  int k = lane;
+  for (; k + 32 < n4; k += 64) {
+    acc0 = CV::dot(a4[k], v4[k], acc0);
+    acc1 = CV::dot(a4[k + 32], v4[k + 32], acc1);
+  }
+  if (k < n4) acc0 = CV::dot(a4[k], v4[k], acc0);
+  return warp_sum(acc0 + acc1);
+}
+
+// one row of a block in global memory against a vector in global memory (FP64), with up to
+// 8 vector loads of the row in flight per lane
+template <typename T>
+__device__ __forceinline__ T coop_row_dot_global(const T* __restrict__ a, const double* v, int m, int lane) {
+  using CV = CoopVec<T>;
+  using V = typename CV::V;
+  constexpr int U = 8;
+  const V* a4 = reinterpret_cast<const V*>(a);
+  const int n4 = m / CV::W;
+  T acc = 0;
+  for (int k0 = 0; k0 < n4; k0 += 32 * U) {
+    V r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * 32 + lane;
+      r[u] = __ldcs(a4 + (k < n4 ? k : 0));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int k = k0 + u * 32 + lane;
+      if (k < n4) acc = CV::dot(r[u], CV::from(v + (size_t)k * CV::W), acc);
+    }
+  }
+  return warp_sum(acc);
+}
+
+__device__ __forceinline__ bool coop_wait(uint32_t addr, uint32_t parity) {
+  for (int i = 0; i < (1 << 22); ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+size_t coop_smem_bytes(int m, int rows_max, size_t elem) {
+  return 16 + (((size_t)m * elem + 15) & ~(size_t)15) + 2 * (size_t)rows_max * m * elem;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+    k_cb_solve_coop(int N, int m, int rows_max, const T* __restrict__ Ut, const T* __restrict__ U,
+                    const T* __restrict__ Dinv, const int* __restrict__ perm, const double* __restrict__ g,
+                    double* rb, double* y, double* w, double* __restrict__ x, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  cg::grid_group grid = cg::this_grid();
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(coop_smem);
+  T* vs = reinterpret_cast<T*>(coop_smem + 16);
+  T* buf = reinterpret_cast<T*>(coop_smem + 16 + (((size_t)m * sizeof(T) + 15) & ~(size_t)15));
+  const size_t mm = (size_t)m * m, bstride = (size_t)rows_max * m;
+  const int G = gridDim.x, c = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp_cta = blockDim.x >> 5;
+  const int r0 = (int)((int64_t)c * m / G), nr = (int)((int64_t)(c + 1) * m / G) - r0;
+  const int n_tasks = 2 * (N - 1);
+  // task k < N - 1: forward step b = k + 1 with U_k^T; task k >= N - 1: backward step
+  // b = 2N - 3 - k with U_b
+  auto task_rows = [&](int k) -> const T* {
+    const T* M = k < N - 1 ? Ut + (size_t)k * mm : U + (size_t)(2 * N - 3 - k) * mm;
+    return M + (size_t)r0 * m;
+  };
+  auto prefetch = [&](int k) {
+    if (k >= n_tasks || nr == 0 || threadIdx.x != 0) return;
+    const uint32_t bar = bar0 + 8 * (k & 1), bytes = (uint32_t)((size_t)nr * m * sizeof(T));
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf + (k & 1) * bstride);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(task_rows(k)), "r"(bytes), "r"(bar)
+                 : "memory");
+  };
+  bool late[2] = {false, false};
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  prefetch(0);
+  prefetch(1);
+  const int64_t rows = (int64_t)N * m;
+  const int64_t tid = (int64_t)c * blockDim.x + threadIdx.x, nthr = (int64_t)G * blockDim.x;
+  for (int64_t t = tid; t < rows; t += nthr) {
+    const int p = perm[t];
+    const double val = p >= 0 ? g[p] : 0.0;
+    rb[t] = val;
+    if (t < m) y[t] = val;
+  }
+  grid.sync();
+  // one recurrence step: out_r = rs_r - (M v)_r for this CTA's rows, M's rows in buffer k & 1
+  auto step = [&](int k, const double* v, const double* rs, double* out) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) vs[i] = (T)__ldcg(v + i);
+    __syncthreads();
+    if (nr > 0 && !coop_wait(bar0 + 8 * (k & 1), (uint32_t)((k >> 1) & 1))) {
+      late[k & 1] = true;
+      if (threadIdx.x == 0) atomicOr(err, 8);
+    }
+    const T* Mb = buf + (k & 1) * bstride;
+    for (int lr = warp; lr < nr; lr += nwarp_cta) {
+      const T d = coop_row_dot(Mb + (size_t)lr * m, vs, m, lane);
+      if (lane == 0) out[r0 + lr] = __ldcg(rs + r0 + lr) - (double)d;
+    }
+    __syncthreads();
+    prefetch(k + 2);
+    grid.sync();
+  };
+  for (int k = 0; k < N - 1; ++k) step(k, y + (size_t)k * m, rb + (size_t)(k + 1) * m, y + (size_t)(k + 1) * m);
+  {
+    const int64_t gwarp = tid >> 5, nwarp = nthr >> 5;
+    for (int64_t t = gwarp; t < rows; t += nwarp) {
+      const int64_t b = t / m, l = t - b * m;
+      const T d = coop_row_dot_global(Dinv + (size_t)b * mm + (size_t)l * m, y + (size_t)b * m, m, lane);
+      if (lane == 0) {
+        w[t] = (double)d;
+        if (b == N - 1) rb[t] = (double)d;   // x_{N-1} = w_{N-1}; rb holds x in block layout from here on
+      }
+    }
+  }
+  grid.sync();
+  for (int k = N - 1; k < n_tasks; ++k) {
+    const int b = 2 * N - 3 - k;
+    step(k, rb + (size_t)(b + 1) * m, w + (size_t)b * m, rb + (size_t)b * m);
+  }
+  for (int64_t t = tid; t < rows; t += nthr) {
+    const int p = perm[t];
+    if (p >= 0) x[p] = __ldcg(rb + t);
+  }
+  // a copy that was late is still owed to this CTA's shared memory: give it a bounded chance
+  for (int j = 0; j < 2; ++j)
+    if (late[j]) coop_wait(bar0 + 8 * j, (uint32_t)(((n_tasks - 1 - ((n_tasks - 1 - j) & 1)) >> 1) & 1));
+}
+
 __global__ void k_cb_scatter(int64_t rows, const int* __restrict__ perm, const double* __restrict__ xb,
                              double* __restrict__ x) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -560,6 +756,32 @@ void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense) {
   LAT_CHECK_LAUNCH();
 }
 
+// CTAs of the cooperative whole-solve launch: one per SM when every CTA fits with its shared
+// memory (the FP64 factors' size, the larger of the two) and the device runs cooperative
+// launches, else 0 (the per-step launches are used)
+int coarse_coop_grid(lat_ctx* h) {
+  int dev = 0, coop = 0, max_shm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+  if (cudaDeviceGetAttribute(&max_shm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+  const int G = h->n_sm, m = h->cb_m;
+  if (G <= 0 || m % 4 != 0) return 0;
+  const int rmax = (int)div_up((int64_t)m, G);
+  const size_t s64 = coop_smem_bytes(m, rmax, sizeof(double)), s32 = coop_smem_bytes(m, rmax, sizeof(float));
+  if (s64 > (size_t)max_shm) return 0;
+  int per_sm32 = 0, per_sm64 = 0;
+  bool ok = cudaFuncSetAttribute(k_cb_solve_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32) ==
+                cudaSuccess &&
+            cudaFuncSetAttribute(k_cb_solve_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_cb_solve_coop<float>, kCoopThreads, s32) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm64, k_cb_solve_coop<double>, kCoopThreads, s64) ==
+                cudaSuccess;
+  cudaGetLastError();   // a refused size is not an error of the library
+  return ok && per_sm32 >= 1 && per_sm64 >= 1 ? G : 0;
+}
+
 // Cluster size and shared memory of the FP64 block-LU sweeps; false when the device runs no
 // cluster of at least 8 CTAs with them (the dense inverse is used then).
 bool coarse_block_plan(lat_ctx* h, bool fallback) {
@@ -613,6 +835,33 @@ void run_coarse_block_solve(lat_ctx* h, const double* g, double* x) {
   const int N = h->cb_n, m = h->cb_m;
   const int64_t rows = (int64_t)N * m;
   const size_t mm = (size_t)m * m;
+  if (h->cb_wide && h->cb_coop_grid > 0) {
+    // one cooperative launch for the whole solve
+    h->cb_r.ensure((size_t)rows);
+    const bool f32 = h->cb_U32.p != nullptr;
+    const int G = h->cb_coop_grid, rmax = (int)div_up((int64_t)m, G);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(kCoopThreads);
+    cfg.dynamicSmemBytes = coop_smem_bytes(m, rmax, f32 ? sizeof(float) : sizeof(double));
+    cfg.stream = h->stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (f32)
+      LAT_LAUNCH(h, LAT_CUDA(cudaLaunchKernelEx(&cfg, k_cb_solve_coop<float>, N, m, rmax, (const float*)h->cb_Ut32.p,
+                                                (const float*)h->cb_U32.p, (const float*)h->cb_Dinv32.p,
+                                                (const int*)h->cb_perm.p, g, h->cb_r.p, h->cb_y.p, h->cb_w.p, x,
+                                                h->flag.p)));
+    else
+      LAT_LAUNCH(h, LAT_CUDA(cudaLaunchKernelEx(&cfg, k_cb_solve_coop<double>, N, m, rmax,
+                                                (const double*)h->cb_Ut.p, (const double*)h->cb_U.p,
+                                                (const double*)h->cb_Dinv.p, (const int*)h->cb_perm.p, g,
+                                                h->cb_r.p, h->cb_y.p, h->cb_w.p, x, h->flag.p)));
+    return;
+  }
   if (h->cb_wide) {
     // y_b = g_b - U_{b-1}^T y_{b-1};  w = D^{-1} y;  x_b = w_b - U_b x_{b+1}
     h->cb_r.ensure((size_t)rows);

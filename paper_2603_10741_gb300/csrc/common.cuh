@@ -136,6 +136,7 @@ struct lat_ctx {
   int cb_n = 0, cb_m = 0;                 // number of blocks, padded block size
   bool cb_solve = false;                  // FP64 coarse solves by block LU (no dense inverse)
   bool cb_wide = false;                   // block-LU steps as full-GPU launches (else cluster sweeps)
+  int cb_coop_grid = -1;                  // CTAs of the cooperative whole-solve launch (0: per-step launches)
   int cb_cluster = 0, cb_pre = 0;         // CTAs per cluster of the sweeps, rows prefetched
   size_t cb_shm = 0;
   DBuf<int64_t> cb_dest;                  // coarse entry -> index in [A blocks | B blocks], -1 skip
@@ -422,6 +423,7 @@ void gj_invert(lat_ctx* h, double* A, int n, int batch, int64_t bs, int neg_bit,
                double* snap = nullptr);
 void run_coarse_blocked(lat_ctx* h, const double* S, int64_t np, bool dense);
 bool coarse_block_plan(lat_ctx* h, bool fallback = false);
+int coarse_coop_grid(lat_ctx* h);
 constexpr int64_t kDenseCoarseLimit = 8192;   // largest padded coarse size N m kept as a dense inverse
 constexpr int kWideSweepRows = 512;           // block-LU steps of larger blocks run over the whole GPU
 constexpr int kTcCells = 128;                 // cells per tensor-core tile (the MMA's N)

@@ -1157,7 +1157,8 @@ void run_prepare_solver(lat_ctx* h, const lat_newton_opts* o, const double* u_gl
   // inverse is kept while it is small; its N^2 m^3 build and N^2 m^2 storage decide beyond that.
   const int64_t np = h->n_primal;
   const int want = o ? o->coarse_block_lu : -1;
-  h->cb_wide = want == 2 || (want != 3 && h->cb_m > kWideSweepRows);
+  h->cb_wide = want == 2 || want == 4 || (want != 3 && h->cb_m > kWideSweepRows);
+  h->cb_coop_grid = h->cb_wide && want != 2 ? coarse_coop_grid(h) : 0;
   h->cb_solve = np > 0 && h->coarse_blocked &&
                 (want >= 1 || (want < 0 && (int64_t)h->cb_n * h->cb_m > kDenseCoarseLimit)) &&
                 (h->cb_wide || coarse_block_plan(h, want == 3));
@@ -1709,11 +1710,12 @@ int run_fgmres(lat_ctx* h, const double* b, double* x, const lat_newton_opts* o,
     total = fgmres_core(h, outer, b, x, false, o->krylov_rtol, o->krylov_max_it, o->krylov_restart, false, block,
                         rel_out);
   }
-  if (h->prec == LAT_MIXED_BF16) {
+  if (h->prec == LAT_MIXED_BF16 || (h->cb_solve && h->cb_wide && h->cb_coop_grid > 0)) {
     int fl = 0;
     LAT_CUDA(cudaMemcpyAsync(&fl, h->flag.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     LAT_CUDA(cudaStreamSynchronize(h->stream));
     LAT_REQUIRE(!(fl & 4), LAT_ETIMEOUT, "a tensor-core wait in the local product gave up");
+    LAT_REQUIRE(!(fl & 8), LAT_ETIMEOUT, "a block-row copy of the cooperative coarse solve did not land");
   }
   return total;
 }
@@ -1779,12 +1781,14 @@ void check_opts(const lat_newton_opts* o) {
   LAT_REQUIRE(o->pcg_rtol >= 0 && o->pcg_rtol < 1, LAT_EINVAL, "pcg_rtol in [0, 1)");
   LAT_REQUIRE(o->interface_precond == 0 || o->interface_precond == 1, LAT_EINVAL, "interface_precond is 0 or 1");
   LAT_REQUIRE(o->max_enrich >= 0 && o->max_enrich <= 6, LAT_EINVAL, "max_enrich in [0, 6]");
-  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 3, LAT_EINVAL, "coarse_block_lu in [-1, 3]");
+  LAT_REQUIRE(o->coarse_block_lu >= -1 && o->coarse_block_lu <= 4, LAT_EINVAL, "coarse_block_lu in [-1, 4]");
   LAT_REQUIRE(o->precond_tangent >= -1 && o->precond_tangent <= 1, LAT_EINVAL, "precond_tangent in {-1, 0, 1}");
   LAT_REQUIRE(o->min_enrich >= 0 && o->min_enrich <= o->max_enrich, LAT_EINVAL, "min_enrich in [0, max_enrich]");
   LAT_REQUIRE(o->inner_its >= 0 && o->inner_its <= 190, LAT_EINVAL, "inner_its in [0, 190]");
   LAT_REQUIRE(o->inner_rtol >= 0 && o->inner_rtol < 1, LAT_EINVAL, "inner_rtol in [0, 1)");
   LAT_REQUIRE(o->snapshot == 0 || o->snapshot == 1, LAT_EINVAL, "snapshot is 0 or 1");
+  LAT_REQUIRE(o->eps_refine >= 0 && o->eps_refine <= 12, LAT_EINVAL, "eps_refine in [0, 12]");
+  LAT_REQUIRE(o->eps_refine_rate > 0 && o->eps_refine_rate <= 1, LAT_EINVAL, "eps_refine_rate in (0, 1]");
 }
 
 // FETI rhs of K du = -r: the assembled residual -r split evenly over the copies of each
@@ -1820,6 +1824,8 @@ extern "C" lat_status lattice_default_opts(lat_handle h, lat_newton_opts* o) {
   o->inner_its = h->prec == LAT_FP64 ? 0 : 20;
   o->inner_rtol = 1e-2;
   o->snapshot = 0;
+  o->eps_refine = 2;
+  o->eps_refine_rate = 0.5;
   return LAT_OK;
 }
 
@@ -1848,10 +1854,12 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     const double r0 = rn;
     const int cap = max_iterations > 0 ? max_iterations : o->newton_max_it;
     int it = 0;
+    double eps = o->eps;
+    bool slow_prev = false;
     while (!(rn <= o->newton_rtol * r0 || rn <= floor) && it < cap) {
       double ta = now_ms();
       h->snap_kind = o->snapshot;
-      select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
+      select_cells(h, u, eps, o->max_nr, o->force_all != 0);
       double tb = now_ms();
       R.t_select_ms += tb - ta;
       prepare_enriched(h, o, u);
@@ -1887,18 +1895,39 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
       R.t_linesearch_ms += now_ms() - td;
       R.armijo_m_max = std::max(R.armijo_m_max, mm);
       if (h->verbose)
-        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e N_r=%d keys=%d enrich=%d indef=%d/%d krylov=%d inner=%lld pcg=%lld (rel %.1e) m=%d%s\n",
-                     it, rn, rn / r0, h->n_r, h->n_keys, h->enrich_level, (int)h->indefinite, (int)h->coarse_indefinite,
+        std::fprintf(stderr, "[lattice] newton it %d |r|=%.3e rel=%.3e eps=%.1e N_r=%d keys=%d enrich=%d indef=%d/%d krylov=%d inner=%lld pcg=%lld (rel %.1e) m=%d%s\n",
+                     it, rn, rn / r0, eps, h->n_r, h->n_keys, h->enrich_level, (int)h->indefinite, (int)h->coarse_indefinite,
                      R.krylov_its_total, (long long)h->inner_its_total, (long long)h->pcg_its_total, rel, mm,
                      accepted ? "" : " REJECTED");
       if (!accepted) {
         // leave u and the residual buffers consistent with u
         run_residual(h, u, h->f_cells.p, h->r_glob.p, nullptr, &neg);
+        if (!o->force_all && R.eps_refinements < o->eps_refine) {
+          // the reduced tangent is too coarse for a descent direction here: the same iterate
+          // again with a tenfold tighter reduced-basis tolerance (more principal cells)
+          ++R.eps_refinements;
+          eps *= 0.1;
+          slow_prev = false;
+          continue;
+        }
         R.r_norm = rn;
+        R.eps_last = eps;
         R.iterations = it;
         throw LatError{LAT_ENOT_CONVERGED, "Armijo line search found no acceptable step"};
       }
       LAT_CUDA(cudaMemcpyAsync(u, ut.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      // two accepted steps in a row that reduce the residual by less than eps_refine_rate: the
+      // reduced tangent limits the (linear) convergence, so the next iteration selects with a
+      // tenfold tighter tolerance (one slow step alone may be the nonlinearity far from the
+      // solution, which a finer tangent would not help)
+      const bool slow = rt > o->eps_refine_rate * rn;
+      if (!o->force_all && slow && slow_prev && R.eps_refinements < o->eps_refine) {
+        ++R.eps_refinements;
+        eps *= 0.1;
+        slow_prev = false;
+      } else {
+        slow_prev = slow;
+      }
       rn = rt;
       floor = 1e-12 * run_norm_all(h, h->r_glob.p);
       ++it;
@@ -1911,6 +1940,7 @@ extern "C" lat_status newton_step(lat_handle h, double* u, int32_t max_iteration
     R.pcg_its_total = (int32_t)h->pcg_its_total;
     R.inner_its_total = (int32_t)h->inner_its_total;
     R.enrich_level = h->enrich_level;
+    R.eps_last = eps;
     R.converged = (rn <= o->newton_rtol * r0 || rn <= floor) ? 1 : 0;
     du.release();
     ut.release();
@@ -1994,9 +2024,9 @@ extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_
     LAT_CUDA(cudaMemsetAsync(lam.p, 0, nd * sizeof(double), h->stream));
     LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     h->snap_kind = o->snapshot;
-    select_cells(h, u, o->eps, o->max_nr, o->force_all != 0);
+    double eps = o->eps;
+    select_cells(h, u, eps, o->max_nr, o->force_all != 0);
     prepare_enriched(h, o, u);
-    R.n_r_last = h->n_r;
     double dn = bnorm;
     R.r0_norm = bnorm;
     int it = 0;
@@ -2013,9 +2043,22 @@ extern "C" lat_status adjoint_gradient(lat_handle h, const double* u, const lat_
       LAT_CUDA(cudaMemcpyAsync(d.p, bF.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
       run_axpy(h, nd, -1.0, y.p, d.p);
       run_mask(h, d.p, d.p, 0);
+      const double prev = dn;
       dn = run_norm_free(h, d.p);
       ++it;
+      // the correction contracts the defect by || I - K~^{-1} K || (a linear iteration): above
+      // eps_refine_rate the reduced tangent is too coarse, and the selection is redone with a
+      // tenfold tighter tolerance
+      if (!o->force_all && dn > o->eps_refine_rate * prev && R.eps_refinements < o->eps_refine &&
+          dn > tol * bnorm) {
+        ++R.eps_refinements;
+        eps *= 0.1;
+        select_cells(h, u, eps, o->max_nr, false);
+        prepare_enriched(h, o, u);
+      }
     }
+    R.n_r_last = h->n_r;
+    R.eps_last = eps;
     R.iterations = it;
     R.r_norm = dn;
     R.converged = (bnorm == 0 || dn <= tol * bnorm) ? 1 : 0;

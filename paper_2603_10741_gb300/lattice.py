@@ -59,7 +59,8 @@ class NewtonOpts(C.Structure):
                 ("armijo_max_m", C.c_int32), ("pcg_rtol", C.c_double), ("interface_precond", C.c_int32),
                 ("max_enrich", C.c_int32), ("coarse_block_lu", C.c_int32), ("precond_tangent", C.c_int32),
                 ("min_enrich", C.c_int32), ("inner_its", C.c_int32), ("inner_rtol", C.c_double),
-                ("snapshot", C.c_int32)]
+                ("snapshot", C.c_int32), ("eps_refine", C.c_int32),
+                ("eps_refine_rate", C.c_double)]
 
 
 class NewtonReport(C.Structure):
@@ -67,7 +68,8 @@ class NewtonReport(C.Structure):
                 ("r_norm", C.c_double), ("n_r_last", C.c_int32), ("krylov_its_total", C.c_int32),
                 ("armijo_m_max", C.c_int32), ("t_residual_ms", C.c_double), ("t_select_ms", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_krylov_ms", C.c_double), ("t_linesearch_ms", C.c_double),
-                ("pcg_its_total", C.c_int32), ("enrich_level", C.c_int32), ("inner_its_total", C.c_int32)]
+                ("pcg_its_total", C.c_int32), ("enrich_level", C.c_int32), ("inner_its_total", C.c_int32),
+                ("eps_refinements", C.c_int32), ("eps_last", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

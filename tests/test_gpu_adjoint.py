@@ -36,10 +36,12 @@ def _oracle_end(name, steps):
     return prob, states
 
 
-def _fd_gradient(lat, case, u_end, theta, cells, h, opts):
+def _fd_gradient(lat, case, u_end, theta, cells, h, opts, log=None):
     """Central differences of J over theta_s for the listed cells, re-converging the end state."""
     out = []
     for s in cells:
+        if log is not None:
+            log("fd cell", int(s))
         vals = []
         for sgn in (1.0, -1.0):
             th = theta.copy()
@@ -139,18 +141,28 @@ def test_cfg5_strut10_adjoint_full_size(L, tmp_path):
     exact FP64 tangent action, the correction solved by FGMRES on the FP64 reduced operator); its
     preconditioner runs with BF16 blocks, as does the load path's (an FP64 preconditioner would
     make each interface iteration ~20x slower on these 2616-DOF local blocks)."""
+    import time
     from paper_2603_10741_gb300 import LAT_MIXED_BF16, solve_load_path
+    t0 = time.time()
+
+    def say(*a):
+        print("[cfg5 %.0f s]" % (time.time() - t0), *a, flush=True)
+
     case = latgen.make_case("strut10")
     lat = L.Lattice.from_case(case, LAT_MIXED_BF16)
     opts = lat.lattice_default_opts()               # Newton to 1e-8 relative, as in the configuration
-    u, reps = solve_load_path(lat, case, opts, checkpoint_dir=str(tmp_path))
+    u, reps = solve_load_path(lat, case, opts, checkpoint_dir=str(tmp_path),
+                              log=lambda k, r: say("step", k, "its", r.iterations, "N_r", r.n_r_last,
+                                                   "eps", r.eps_last, "refinements", r.eps_refinements))
     # the perturbed end states: 1e-8 of a residual that is itself O(h) after the perturbation
     opts_fd = lat.lattice_default_opts()
     g, J, rep = lat.adjoint_gradient(u, opts_fd)
+    say("adjoint", rep.as_dict())
     assert rep.converged
     g = g.cpu().numpy()
     cells = np.random.default_rng(5).choice(1000, 20, replace=False)
-    fd = _fd_gradient(lat, case, u, np.asarray(case.mu_scale, dtype=float), cells, 1e-6, opts_fd)
+    fd = _fd_gradient(lat, case, u, np.asarray(case.mu_scale, dtype=float), cells, 1e-6, opts_fd, log=say)
+    say("fd", np.abs(fd - g[cells]).max() / np.abs(g).max())
     assert np.abs(fd - g[cells]).max() < 1e-5 * np.abs(g).max(), (fd, g[cells])
     step, _, u14, u13 = lat.lattice_checkpoint_load(tmp_path / "step_0014.ckpt")
     lat2 = L.Lattice.from_case(case, LAT_MIXED_BF16)
@@ -158,5 +170,6 @@ def test_cfg5_strut10_adjoint_full_size(L, tmp_path):
     assert torch.equal(u, u_res)
     g2, _, _ = lat2.adjoint_gradient(u_res, opts_fd)
     assert np.array_equal(g, g2.cpu().numpy())
+    say("resumed from step 14: identical displacement and gradient")
     lat.close()
     lat2.close()

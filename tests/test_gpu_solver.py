@@ -232,11 +232,44 @@ def test_newton_bf16_mode_ring4(L):
     lat.close()
 
 
+def test_tolerance_tightening_on_slow_reduced_newton(L):
+    """ring4, FP64, three load steps from a greedy tolerance of 0.05 (one principal cell: the
+    first greedy residual is 0.115 and all cells share one snapshot at the affine predictor),
+    with eps_refine = 3 and a contraction test of 1e-3 (two steps in a row that reduce the
+    residual by less than 1000x count as slow): eps is divided by 10 at least once, every
+    report's eps_last is 0.05 10^-k for its k tightenings, and the load path still reaches the
+    oracle's solution.  With eps_refine = 0 eps stays at 0.05."""
+    from paper_2603_10741_gb300 import solve_load_path
+    from paper_2603_10741_gb300.lattice import LatticeError
+    case = latgen.make_case("ring4")
+    prob = Problem(case)
+    ref, _ = ON.load_path(prob, n_steps=3, tol=1e-12)
+    for refine in (3, 0):
+        lat = L.Lattice.from_case(case)
+        opts = lat.lattice_default_opts(newton_rtol=1e-11, krylov_rtol=1e-12, eps=0.05, eps_refine=refine,
+                                        eps_refine_rate=1e-3, newton_max_it=100)
+        try:
+            u, reps = solve_load_path(lat, case, opts, steps=3)
+        except (LatticeError, RuntimeError):
+            assert refine == 0                 # a rejected direction ends the call when eps is fixed
+            lat.close()
+            continue
+        err = np.linalg.norm(u.cpu().numpy() - ref[-1]) / np.linalg.norm(ref[-1])
+        assert err < 1e-9, (refine, err)
+        for r in reps:
+            assert r["eps_refinements"] <= refine
+            assert abs(r["eps_last"] - 0.05 * 10.0 ** -r["eps_refinements"]) < 1e-12 * 0.05, r
+        if refine:
+            assert sum(r["eps_refinements"] for r in reps) >= 1, reps
+        lat.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_blocked_coarse_inverse_matches_dense(L, precision):
     """Coarse solves on the 8x8 ring lattice: the block-LU sweeps over the cell layers (one
     16-CTA cluster per sweep with prefetched rows; one 8-CTA cluster reading rows from global
-    memory; one whole-GPU launch per step) and the block-tridiagonal explicit
+    memory; one whole-GPU launch per step; the whole solve as one cooperative launch) and the
+    block-tridiagonal explicit
     inverse equal the dense inverse of the unlayered coarse matrix, and
     with every cell principal K^-rom stays the exact inverse of K~ in FP64.  In the FP32 mode
     (FP32 local inverses; the block-LU solve stays FP64, the explicit inverse is applied as an FP32
@@ -247,7 +280,7 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
     arrays = L.case_arrays(case)
     outs = []
     tol = 1e-9 if precision == 0 else 1e-5
-    for layered, block_lu in ((True, 1), (True, 2), (True, 3), (True, 0), (False, 0)):
+    for layered, block_lu in ((True, 1), (True, 2), (True, 3), (True, 4), (True, 0), (False, 0)):
         a = dict(arrays)
         if not layered:
             a["cell_layer"] = None
@@ -270,9 +303,9 @@ def test_blocked_coarse_inverse_matches_dense(L, precision):
             assert err < 1e-9, (layered, block_lu, err)
         outs.append(back[:nd].cpu().numpy())
         lat.close()
-    ref = np.abs(outs[4]).max()
-    for k in range(3):
-        assert np.abs(outs[k] - outs[4]).max() < tol * ref, k
+    ref = np.abs(outs[5]).max()
+    for k in range(4):
+        assert np.abs(outs[k] - outs[5]).max() < tol * ref, k
     assert np.abs(outs[3] - outs[4]).max() < (1e-10 if precision == 0 else tol) * ref
 
 
