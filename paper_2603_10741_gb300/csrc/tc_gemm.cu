@@ -335,12 +335,14 @@ __global__ void k_pack_lam(int n_cells, int n_D, int KP, const double* __restric
     float v = 0.f;
     if (pos < c_end && gk < n_D) {
       const size_t q = (size_t)gk * n_cells + perm[pos];
+      // formed in FP32 (the value is rounded to FP32 and split into a BF16 pair anyway): only
+      // the two multiplier reads convert from FP64, the FP64 pipe being the narrow one here
       const int2 l = lk[q];
-      double a = 0.0;
-      if (l.x) a += (l.x > 0 ? 1.0 : -1.0) * lam[abs(l.x) - 1];
-      if (l.y) a += (l.y > 0 ? 1.0 : -1.0) * lam[abs(l.y) - 1];
-      if (lsc) a *= (double)lsc[q];
-      v = (float)a;
+      float a = 0.f;
+      if (l.x) a = l.x > 0 ? __double2float_rn(lam[l.x - 1]) : -__double2float_rn(lam[-l.x - 1]);
+      if (l.y) a += l.y > 0 ? __double2float_rn(lam[l.y - 1]) : -__double2float_rn(lam[-l.y - 1]);
+      if (lsc) a *= lsc[q];
+      v = a;
     }
     const __nv_bfloat16 h = __float2bfloat16(v);
     hi[core_off(c, k)] = h;
