@@ -132,7 +132,7 @@ def test_compliance_autograd_function(L):
 
 
 @pytest.mark.skipif(os.environ.get("LATTICE_CFG5") != "1",
-                    reason="full-size adjoint run (about 10 minutes of GPU time): set LATTICE_CFG5=1")
+                    reason="full-size adjoint run (more than 30 minutes of GPU time): set LATTICE_CFG5=1")
 def test_cfg5_strut10_adjoint_full_size(L, tmp_path):
     """The adjoint configuration at full size: 10 x 10 x 10 strut cells at -15 % in 15 steps, the
     gradient w.r.t. the 1 000 per-cell factors, with a checkpoint after every load step; central
