@@ -20,9 +20,13 @@
 //   w_i = D_i^{-1} y_i                                 (all blocks at once)
 //   x_{N-1} = w_{N-1},   x_i = w_i - U_i x_{i+1}
 // which is 3 N m^2 multiply-adds per solve instead of N^2 m^2.  The two sweeps are sequential
-// in i; each runs in one thread-block cluster (16 CTAs where the device allows it, else 8) that
-// splits the m rows of every step, prefetches the next step's rows with cp.async and exchanges
-// the new block vector through distributed shared memory, one cluster barrier per step.
+// in i.  For blocks of up to 512 rows each sweep runs in one thread-block cluster (16 CTAs where
+// the device allows it, else 8) that splits the m rows of every step, prefetches the next step's
+// rows with cp.async and exchanges the new block vector through distributed shared memory, one
+// cluster barrier per step.  Larger blocks do not stream fast enough through one cluster: there
+// the whole solve is one cooperative launch over every SM (k_cb_solve_coop, a grid barrier per
+// step, each CTA's rows of the next blocks brought in by bulk copies ahead of time), or on
+// request one launch per step (k_cb_step, k_cb_step32).
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -135,7 +135,7 @@ struct lat_ctx {
   bool coarse_blocked = false;
   int cb_n = 0, cb_m = 0;                 // number of blocks, padded block size
   bool cb_solve = false;                  // FP64 coarse solves by block LU (no dense inverse)
-  bool cb_wide = false;                   // block-LU steps as full-GPU launches (else cluster sweeps)
+  bool cb_wide = false;                   // block-LU solves over the whole GPU (else cluster sweeps)
   int cb_coop_grid = -1;                  // CTAs of the cooperative whole-solve launch (0: per-step launches)
   int cb_cluster = 0, cb_pre = 0;         // CTAs per cluster of the sweeps, rows prefetched
   size_t cb_shm = 0;
