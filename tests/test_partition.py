@@ -1,9 +1,10 @@
-"""Cell-slab partition and FETI-DP exchange plan over several ranks (CPU, gloo, world size 2).
+"""Cell-slab partition and FETI-DP exchange plan over several ranks (CPU, gloo, 2 and 3 ranks).
 
 The sharded saddle-point operator [K~ B^T; B 0] and the sharded dot product (the two pieces of a
 Krylov iteration that couple ranks), assembled from the exchange plan with point-to-point halo
 messages and sum all-reduces, must equal the single-rank operator and dot of the oracle's
-FETI-DP system (Section 3.3.1) on the same vector."""
+FETI-DP system (Section 3.3.1) on the same vector; flexible GMRES iterations built from them
+must give the single-rank iterate and residual history."""
 import os
 import socket
 import sys
@@ -84,140 +85,242 @@ def _free_port():
     return port
 
 
-def _rank_main(rank, world, port, name, out):
-    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
-    sys.path.insert(0, ROOT)
-    import torch
-    import torch.distributed as dist
-    from paper_2603_10741_gb300 import partition as P
-    dist.init_process_group("gloo", rank=rank, world_size=world)
-    prob, K, fe, idx, A, lay, layer = _system(name)
-    cell = prob.cell
-    n_cells, n_loc = lay.n_cells, lay.n_loc
-    n_r, n_p, L = fe.n_r, fe.n_p, fe.n_lambda
-    plan = P.exchange_plans(lay, P.slab_partition(layer, world))[rank]
-    # the same seeded saddle-point vector on every rank, in the oracle's numbering
-    rng = np.random.default_rng(31)
-    v = rng.uniform(-1, 1, n_r + n_p + L)
-    # its cell-stacked image: local part (remaining rows), replicated primal part, multipliers
-    xloc = np.zeros(n_loc * n_cells)
-    s_of, k_of = np.nonzero(fe.r_index >= 0)
-    xloc[k_of * n_cells + s_of] = v[fe.r_index[s_of, k_of]]
-    vP = v[n_r:n_r + n_p]
-    lam = v[n_r + n_p:]
-    p_of = -np.ones(prob.n_dof, dtype=np.int64)
-    p_of[lay.primal_dofs] = np.arange(n_p)
+class _Shard:
+    """One rank's share of the FETI-DP saddle-point system of `name` under the slab partition:
+    its cells' local rows, the replicated primal part and its owned multipliers.  A sharded
+    vector is a full-length array [local n_loc*n_cells | primal n_p | multipliers n_lambda] in
+    which only this rank's entries are meaningful (the rest stay zero)."""
 
-    def exchange(vals_for_peer, peers_recv):
+    def __init__(self, rank, world, name):
+        import torch.distributed as dist
+        from paper_2603_10741_gb300 import partition as P
+        self.dist = dist
+        self.rank = rank
+        prob, K, fe, idx, A, lay, layer = _system(name)
+        self.prob, self.K, self.fe, self.idx, self.A, self.lay = prob, K, fe, idx, A, lay
+        self.cell = prob.cell
+        self.n_cells, self.n_loc = lay.n_cells, lay.n_loc
+        self.n_r, self.n_p, self.L = fe.n_r, fe.n_p, fe.n_lambda
+        self.rank_of_cell = P.slab_partition(layer, world)
+        self.plan = P.exchange_plans(lay, self.rank_of_cell)[rank]
+        self.p_of = -np.ones(prob.n_dof, dtype=np.int64)
+        self.p_of[lay.primal_dofs] = np.arange(self.n_p)
+        nl = self.n_loc * self.n_cells
+        self.nl = nl
+        own = np.zeros(nl, dtype=bool)
+        for s in self.plan.cells:
+            own[np.arange(self.n_loc) * self.n_cells + s] = True
+        self.own_loc = own
+        self.own_lam = np.zeros(self.L, dtype=bool)
+        self.own_lam[self.plan.lam_owned] = True
+        # oracle remaining unknown <-> cell-stacked entry
+        self.s_of, self.k_of = np.nonzero(fe.r_index >= 0)
+        self.entry_of_r = self.k_of * self.n_cells + self.s_of
+
+    def P_rank(self, l):
+        return self.rank_of_cell[self.lay.cell_of_second[l]]
+
+    def to_stacked(self, v):
+        """A vector in the oracle's numbering -> its cell-stacked image (every entry)."""
+        w = np.zeros(self.nl + self.n_p + self.L)
+        w[self.entry_of_r] = v[self.fe.r_index[self.s_of, self.k_of]]
+        w[self.nl:self.nl + self.n_p] = v[self.n_r:self.n_r + self.n_p]
+        w[self.nl + self.n_p:] = v[self.n_r + self.n_p:]
+        return w
+
+    def to_oracle(self, w):
+        v = np.zeros(self.n_r + self.n_p + self.L)
+        v[self.fe.r_index[self.s_of, self.k_of]] = w[self.entry_of_r]
+        v[self.n_r:] = w[self.nl:]
+        return v
+
+    def restrict(self, w):
+        """Keep this rank's entries of a cell-stacked vector (primal part replicated)."""
+        out = w.copy()
+        out[:self.nl][~self.own_loc] = 0.0
+        out[self.nl + self.n_p:][~self.own_lam] = 0.0
+        return out
+
+    def exchange(self, vals_for_peer, peers_recv):
         """Point-to-point halo: send vals_for_peer[q] to q, receive len(peers_recv[q]) from q."""
+        import torch
         reqs, got = [], {}
         for q, arr in vals_for_peer.items():
-            reqs.append(dist.isend(torch.tensor(arr, dtype=torch.float64), q))
+            reqs.append(self.dist.isend(torch.tensor(arr, dtype=torch.float64), q))
         for q, cnt in peers_recv.items():
             buf = torch.zeros(cnt, dtype=torch.float64)
-            reqs.append(dist.irecv(buf, q))
+            reqs.append(self.dist.irecv(buf, q))
             got[q] = buf
         for r in reqs:
             r.wait()
         return {q: b.numpy() for q, b in got.items()}
 
-    def sharded_apply(xloc, vP, lam):
-        """w = A v on this rank's cells, owned multipliers and the replicated primal part."""
-        wloc = np.zeros_like(xloc)
-        gP = np.zeros(n_p)
-        cd = prob.cell_dofs
+    def apply(self, w):
+        """A w on this rank: owned local rows, the replicated primal part (one sum all-reduce),
+        owned multipliers; halo messages for B x and B^T lambda."""
+        import torch
+        lay, plan, n_cells, n_loc = self.lay, self.plan, self.n_cells, self.n_loc
+        xloc, vP, lam = w[:self.nl], w[self.nl:self.nl + self.n_p], w[self.nl + self.n_p:]
+        wloc = np.zeros(self.nl)
+        gP = np.zeros(self.n_p)
+        cd = self.prob.cell_dofs
         for s in plan.cells:
-            Kd = cell.dense(K[s])
+            Kd = self.cell.dense(self.K[s])
             xs = np.zeros(n_loc)
             for k in range(n_loc):
-                i = idx[s, k]
+                i = self.idx[s, k]
                 if i < 0:
                     continue
-                xs[k] = xloc[k * n_cells + s] if i < n_r else vP[i - n_r]
+                xs[k] = xloc[k * n_cells + s] if i < self.n_r else vP[i - self.n_r]
             ys = Kd @ xs
             for k in range(n_loc):
-                i = idx[s, k]
+                i = self.idx[s, k]
                 if i < 0:
                     continue
-                if i < n_r:
+                if i < self.n_r:
                     wloc[k * n_cells + s] += ys[k]
                 else:
-                    gP[p_of[cd[s, k]]] += ys[k]
+                    gP[self.p_of[cd[s, k]]] += ys[k]
         # primal assembly: one sum all-reduce (replicated coarse part)
         t = torch.tensor(gP)
-        dist.all_reduce(t)
+        self.dist.all_reduce(t)
         wP = t.numpy()
         # B^T lambda: first copies are local; second copies of owned multipliers on other ranks
         # are sent there, and multipliers of other ranks with a second copy here are received
-        wloc_t = wloc
         for l in plan.lam_owned:
-            wloc_t[lay.copies_first[l]] += lam[l]
-            if P_rank(l) == rank:
-                wloc_t[lay.copies_second[l]] -= lam[l]
-        got = exchange({q: lam[ls] for q, ls in plan.recv_lam.items()},
-                       {q: len(ls) for q, ls in plan.send_lam.items()})
+            wloc[lay.copies_first[l]] += lam[l]
+            if self.P_rank(l) == self.rank:
+                wloc[lay.copies_second[l]] -= lam[l]
+        got = self.exchange({q: lam[ls] for q, ls in plan.recv_lam.items()},
+                            {q: len(ls) for q, ls in plan.send_lam.items()})
         for q, vals in got.items():
             for l, val in zip(plan.send_lam[q], vals):
-                wloc_t[lay.copies_second[l]] -= val
+                wloc[lay.copies_second[l]] -= val
         # B x: owned multipliers, second copies from their ranks
-        got = exchange({q: xloc[lay.copies_second[ls]] for q, ls in plan.send_lam.items()},
-                       {q: len(ls) for q, ls in plan.recv_lam.items()})
+        got = self.exchange({q: xloc[lay.copies_second[ls]] for q, ls in plan.send_lam.items()},
+                            {q: len(ls) for q, ls in plan.recv_lam.items()})
         second = {}
         for q, vals in got.items():
             second.update(zip(plan.recv_lam[q].tolist(), vals.tolist()))
-        wl = {}
+        wl = np.zeros(self.L)
         for l in plan.lam_owned:
-            sv = xloc[lay.copies_second[l]] if P_rank(l) == rank else second[int(l)]
-            wl[int(l)] = xloc[lay.copies_first[l]] - sv
-        return wloc_t, wP, wl
+            sv = xloc[lay.copies_second[l]] if self.P_rank(l) == self.rank else second[int(l)]
+            wl[l] = xloc[lay.copies_first[l]] - sv
+        out = np.concatenate([wloc, wP, wl])
+        return self.restrict(out)
 
-    rank_of_cell = P.slab_partition(layer, world)
+    def dot(self, a, b):
+        """Sharded dot product: owned local rows and multipliers, the primal part on rank 0 only,
+        one sum all-reduce."""
+        import torch
+        d = float(a[:self.nl][self.own_loc] @ b[:self.nl][self.own_loc])
+        d += float(a[self.nl + self.n_p:][self.own_lam] @ b[self.nl + self.n_p:][self.own_lam])
+        if self.plan.primal_root:
+            d += float(a[self.nl:self.nl + self.n_p] @ b[self.nl:self.nl + self.n_p])
+        t = torch.tensor([d], dtype=torch.float64)
+        self.dist.all_reduce(t)
+        return t.item()
 
-    def P_rank(l):
-        return rank_of_cell[lay.cell_of_second[l]]
 
-    wloc, wP, wl = sharded_apply(xloc, vP, lam)
-    # gather the sharded result on every rank and compare with the single-rank operator
-    mine = {"loc": {int(e): float(wloc[e]) for s in plan.cells for e in (np.arange(n_loc) * n_cells + s)},
-            "lam": wl}
-    allp = [None] * world
-    dist.all_gather_object(allp, mine)
-    ref = A @ v
-    ref_loc = np.zeros(n_loc * n_cells)
-    ref_loc[k_of * n_cells + s_of] = ref[fe.r_index[s_of, k_of]]
-    err = 0.0
-    for part in allp:
-        for e, val in part["loc"].items():
-            err = max(err, abs(val - ref_loc[e]))
-        for l, val in part["lam"].items():
-            err = max(err, abs(val - ref[n_r + n_p + l]))
-    err = max(err, np.abs(wP - ref[n_r:n_r + n_p]).max())
-    scale = np.abs(ref).max()
-    # sharded dot <v, A v>: owned local rows + owned multipliers, primal part on rank 0, one sum
-    d = sum(xloc[k * n_cells + s] * wloc[k * n_cells + s] for s in plan.cells for k in range(n_loc))
-    d += sum(lam[l] * wl[int(l)] for l in plan.lam_owned)
-    if plan.primal_root:
-        d += float(vP @ wP)
-    t = torch.tensor([d], dtype=torch.float64)
-    dist.all_reduce(t)
-    out[rank] = (err / scale, abs(t.item() - v @ ref) / abs(v @ ref), len(plan.cells),
-                 sum(len(x) for x in plan.recv_lam.values()))
+def _jacobi(sh):
+    """A preconditioner local to every rank: the inverse diagonal of the cells' tangents on the
+    local rows (a cell-stacked entry belongs to one cell), identity on the primal part and the
+    multipliers."""
+    d = np.ones(sh.nl + sh.n_p + sh.L)
+    for s in range(sh.n_cells):
+        Kd = sh.cell.dense(sh.K[s])
+        for k in range(sh.n_loc):
+            i = sh.idx[s, k]
+            if 0 <= i < sh.n_r:
+                d[k * sh.n_cells + s] = 1.0 / Kd[k, k]
+    return d
+
+
+def _fgmres(apply, dot, prec, b, m):
+    """m iterations of right-preconditioned flexible GMRES from x = 0, classical Gram-Schmidt
+    applied twice; returns x_m and the least-squares residual norms."""
+    beta = np.sqrt(dot(b, b))
+    V, Z = [b / beta], []
+    H = np.zeros((m + 1, m))
+    res = [beta]
+    y = None
+    for j in range(m):
+        z = prec(V[j])
+        Z.append(z)
+        w = apply(z)
+        for _ in range(2):
+            h = np.array([dot(w, V[i]) for i in range(j + 1)])
+            for i in range(j + 1):
+                w = w - h[i] * V[i]
+            H[:j + 1, j] += h
+        H[j + 1, j] = np.sqrt(dot(w, w))
+        V.append(w / H[j + 1, j])
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        res.append(float(np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y)))
+    x = sum(y[i] * Z[i] for i in range(m))
+    return x, res
+
+
+def _rank_main(rank, world, port, name, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sh = _Shard(rank, world, name)
+    # the same seeded saddle-point vector on every rank, in the oracle's numbering
+    rng = np.random.default_rng(31)
+    v = rng.uniform(-1, 1, sh.n_r + sh.n_p + sh.L)
+    w = sh.apply(sh.restrict(sh.to_stacked(v)))
+    ref = sh.A @ v
+    ref_w = sh.restrict(sh.to_stacked(ref))
+    err = np.abs(w - ref_w).max() / np.abs(ref).max()
+    d = sh.dot(sh.restrict(sh.to_stacked(v)), w)
+    out[rank] = (err, abs(d - v @ ref) / abs(v @ ref), len(sh.plan.cells),
+                 sum(len(x) for x in sh.plan.recv_lam.values()))
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["ring4", "strut2"])
-def test_sharded_saddle_point_operator_two_gloo_ranks(name):
+def _fgmres_rank_main(rank, world, port, name, m, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sh = _Shard(rank, world, name)
+    rng = np.random.default_rng(41)
+    b = rng.uniform(-1, 1, sh.n_r + sh.n_p + sh.L)
+    dj = _jacobi(sh)
+    x, res = _fgmres(sh.apply, sh.dot, lambda r: sh.restrict(dj * r), sh.restrict(sh.to_stacked(b)), m)
+    # gather this rank's entries into the oracle's numbering on every rank
+    parts = [None] * world
+    dist.all_gather_object(parts, (sh.own_loc, sh.own_lam, x))
+    full = np.zeros_like(x)
+    for own_loc, own_lam, xp in parts:
+        full[:sh.nl][own_loc] = xp[:sh.nl][own_loc]
+        full[sh.nl + sh.n_p:][own_lam] = xp[sh.nl + sh.n_p:][own_lam]
+    full[sh.nl:sh.nl + sh.n_p] = x[sh.nl:sh.nl + sh.n_p]
+    out[rank] = (sh.to_oracle(full), res)
+    dist.destroy_process_group()
+
+
+def _spawn(target, world, *args):
     port = _free_port()
     ctx = mp.get_context("spawn")
     mgr = ctx.Manager()
     out = mgr.dict()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, name, out)) for r in range(2)]
+    procs = [ctx.Process(target=target, args=(r, world, port) + args + (out,)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(300)
         assert p.exitcode == 0
-    res = dict(out)
+    return dict(out)
+
+
+@pytest.mark.parametrize("name", ["ring4", "strut2"])
+def test_sharded_saddle_point_operator_two_gloo_ranks(name):
+    res = _spawn(_rank_main, 2, name)
     for r in range(2):
         op_err, dot_err, n_cells, n_halo = res[r]
         assert op_err < 1e-13, (r, op_err)
@@ -225,3 +328,29 @@ def test_sharded_saddle_point_operator_two_gloo_ranks(name):
         assert n_cells > 0
     # the slab boundary cuts interfaces: rank 0 owns multipliers whose second copy is on rank 1
     assert res[0][3] > 0
+
+
+@pytest.mark.parametrize("name,world", [("ring4", 2), ("strut2", 2), ("ring4", 3)])
+def test_sharded_fgmres_iterations_equal_single_rank(name, world):
+    """Eight flexible GMRES iterations on the saddle-point system [K~ B^T; B 0] with a
+    preconditioner local to every rank (inverse cell diagonals on the local rows), run sharded over
+    gloo ranks (halo messages inside the operator, one all-reduce per dot, replicated primal
+    part), give the same iterate and the same residual history as the single-rank iteration on
+    the assembled oracle system."""
+    m = 8
+    res = _spawn(_fgmres_rank_main, world, name, m)
+    prob, K, fe, idx, A, lay, layer = _system(name)
+    rng = np.random.default_rng(41)
+    b = rng.uniform(-1, 1, fe.n_r + fe.n_p + fe.n_lambda)
+    # the same preconditioner in the oracle's numbering: inverse diagonal of the owning cell's
+    # tangent on every remaining unknown (each belongs to one cell), identity elsewhere
+    dj = np.ones_like(b)
+    s_of, k_of = np.nonzero(fe.r_index >= 0)
+    for s, k in zip(s_of, k_of):
+        dj[fe.r_index[s, k]] = 1.0 / prob.cell.dense(K[s])[k, k]
+    x_ref, res_ref = _fgmres(lambda v: A @ v, lambda a, c: float(a @ c), lambda r: dj * r, b, m)
+    assert res_ref[-1] < 0.9 * res_ref[0]           # the iteration makes progress
+    for r in range(world):
+        x, hist = res[r]
+        assert np.abs(x - x_ref).max() < 1e-10 * np.abs(x_ref).max(), r
+        assert np.allclose(hist, res_ref, rtol=1e-10, atol=0), r
