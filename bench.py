@@ -204,8 +204,8 @@ def oracle_apply_fn(case_name, load_step, n_sample):
     def step():
         return OR.reduced_apply(prob.cell, Kp, alpha, X)
 
-    desc = ("oracle reduced tangent action (numpy, %d dense principal matrices) on the first %d cells of %s "
-            "at the affine predictor of load step %d" % (len(g.S), n, case_name, load_step))
+    desc = ("oracle reduced action (numpy, %d dense principals), first %d cells of %s, predictor of step %d"
+            % (len(g.S), n, case_name, load_step))
     return step, prob.cell.n_nodes * prob.d * n, desc
 
 
@@ -463,14 +463,14 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.case],
                    "precision": {"fp64": "FP64 reduced (EIM) path",
-                                 "fp32": "mixed: FP32 reduced action (inner Krylov) and FP32 preconditioner blocks, "
-                                         "FP64 residual, outer operator and update",
-                                 "bf16": "mixed: FP32 reduced action (inner Krylov), BF16 principal blocks with FP32 "
-                                         "accumulation, FP64 residual, outer operator and update"}[args.precision],
+                                 "fp32": "FP32 action (inner Krylov) and preconditioner; FP64 residual, "
+                                         "outer operator, update",
+                                 "bf16": "FP32 action (inner Krylov), BF16-pair preconditioner blocks; FP64 "
+                                         "residual, outer operator, update"}[args.precision],
                    "step": "one Newton iteration (all hot-path rows) from the predictor of load step %d"
                            % (args.state_step + 1),
-                   "value": "%s GDOF/s: n_loc*N_s stacked DOF per second of the %d tangent-action launches "
-                            "inside the timed iterations" % (apply_name, n_apply),
+                   "value": "%s: n_loc*N_s DOF/s over its %d launches in the timed iterations"
+                            % (apply_name, n_apply),
                    "l2": "inputs larger than L2: cell vectors %.0f MB each, FGMRES bases %.0f MB"
                          % (4 * stacked / 1e6, 8.0 * (2 * opts.krylov_restart + 2 * opts.inner_its + 3) * s.n_krylov
                             / 1e6),
@@ -488,8 +488,8 @@ def run_ours(args):
     # H2D copy of the cell vector from pinned memory and the D2H copy of the result per step
     out["e2e"] = bench_e2e(lat, args, ws, dev, u_start, stacked, args.precision)
     if not args.quick and rank == 0:
-        out["vs_plain_fp64"] = plain_vs_reduced("ring32", 1)
-        detail["vs_plain_fp64"] = out["vs_plain_fp64"]
+        detail["vs_plain_fp64"] = plain_vs_reduced("ring32", 1)
+        out["vs_plain_fp64"] = vs_plain_summary(detail["vs_plain_fp64"])
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     lat.close()
@@ -580,8 +580,16 @@ def bench_e2e(lat, args, ws, dev, u_start, stacked, precision):
     nb = host_x.numel() * host_x.element_size()
     return {"value": ws * stacked / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms,
             "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "n_r": sel["n_r"],
-            "what": "apply_reduced_tangent with the cell vector copied from pinned host memory and the result "
-                    "copied back, every call"}
+            "what": "apply_reduced_tangent, X from pinned host memory and Y back every call"}
+
+
+def vs_plain_summary(vp):
+    """The line's short form of plain_vs_reduced's result (the full one goes to --detail)."""
+    paths = ("plain_fp64", "reduced_fp64", "reduced_mixed_fp32")
+    return {"workload": vp["workload"].split(":")[0] + " load step %d, each path to newton_rtol 1e-8" % vp["load_step"],
+            "ms_per_load_step": {p: vp[p]["ms_per_load_step"] for p in paths},
+            "converged": all(vp[p]["converged"] for p in paths),
+            "speedup_reduced_fp64": vp["speedup_reduced_fp64"], "speedup_reduced_mixed": vp["speedup_reduced_mixed"]}
 
 
 def plain_vs_reduced(case_name, load_step):
