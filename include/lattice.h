@@ -293,8 +293,11 @@ lat_status lattice_default_opts(lat_handle h, lat_newton_opts* opts);
 /* Newton-Raphson for one load step (Section 2.2.5) from the initial guess in u_glob (dev,
  * in/out, Dirichlet values already set): residual, principal selection, FETI-DP setup,
  * FGMRES on the saddle-point system with the reduced tangent, Armijo line search (beta = 1/2,
- * c = 1e-4), update; until ||r_F||/||r_F(u^0)|| <= newton_rtol.  max_iterations > 0 limits
- * the iterations of this call (a call with max_iterations = 1 runs exactly one iteration). */
+ * c = 1e-4), update; until ||r_F||/||r_F(u^0)|| <= newton_rtol.  A rejected direction (no
+ * acceptable step within armijo_max_m halvings) repeats the iteration with a tighter greedy
+ * tolerance while opts->eps_refine allows, else the call returns LAT_ENOT_CONVERGED with u_glob
+ * unchanged from its last accepted iterate.  max_iterations > 0 limits the iterations of this
+ * call (a call with max_iterations = 1 runs exactly one iteration). */
 lat_status newton_step(lat_handle h, double* u_glob, int32_t max_iterations,
                        const lat_newton_opts* opts, lat_newton_report* report);
 
