@@ -75,3 +75,30 @@ def test_compact_line_is_short_and_complete():
     assert back["roofline"]["traffic"] is None and "workload" in back["config"]
     for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
         assert k in back["e2e"]
+
+
+def test_work_models_of_the_roofline_entries():
+    """The algorithmic work the roofline entries divide by, for the 20^3 strut lattice's sizes:
+    the FP32 reduced action streams X and Y once plus alpha and one principal's values, 4 (2 n_loc
+    N_s + N_r N_s + N_r nnz) bytes; the mixed-mode coarse block-LU solve streams the FP32 factors
+    U, U^T (N - 1 blocks each) and D^{-1} (N blocks) once, 4 (3 N - 2) m^2 bytes; the dual-block
+    product is 2 (n_D + n_P) n_D flops per cell."""
+    import types
+
+    import bench
+    import latgen
+    cell_nodes = latgen.strut_cell(12, 0.15)[0].shape[0]
+    assert cell_nodes == 880
+    s = types.SimpleNamespace(n_cells=8000, n_loc=3 * cell_nodes, nnz=122112, n_r_local=2616, n_p_local=24,
+                              n_i_local=924, n_coarse_blocks=19, coarse_block=1324, n_primal=24000)
+    w, kind = bench.kernel_work("apply_reduced_fp32", s, 1, True)
+    assert kind == "hbm" and w == 4 * (2 * 2640 * 8000 + 8000 + 122112) == 169480448
+    w, kind = bench.kernel_work("coarse_solve", s, 1, True)
+    assert kind == "hbm" and w == 4 * 55 * 1324 ** 2
+    w, kind = bench.kernel_work("coarse_solve", s, 1, False)
+    assert kind == "fp64" and w == 2 * 55 * 1324 ** 2
+    n_d = 2616 - 924
+    w, kind = bench.kernel_work("local_tc_dual", s, 1, True)
+    assert kind == "tensor" and w == 2.0 * (n_d + 24) * n_d * 8000
+    w, kind = bench.kernel_work("dual_schur_tc", s, 1, True)
+    assert kind == "tensor" and w == 2.0 * n_d * n_d * 8000
